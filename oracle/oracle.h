@@ -1,0 +1,172 @@
+/*
+ * oracle.h -- plain, sequential CPU oracle for the Swendsen-Wang sweep of the
+ * two-dimensional classical XY model with Wolff's embedded-Ising reflection.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA path, never
+ * to stand in for it: only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header, table or constant
+ * generator with the CUDA library; both sides implement Philox4x32-10
+ * independently from its published definition (Salmon, Moraes, Dror, Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ *
+ * Model (the paper's Eq. (3)): H = -J sum_<ij> cos(theta_i - theta_j), J = 1,
+ * nearest neighbours of an Lx x Ly square lattice, site index i = y*Lx + x.
+ * Each direction can be periodic or open (open is used only for the 1D chain
+ * checks: Ly = 1, open x).
+ *
+ * One sweep t (one MCS) is, in order:
+ *   1. axis:  phi from Philox domain AXIS, r = (cos phi, sin phi),
+ *             C = (pi + 2 phi) mod 2 pi, C32 = (float)C.
+ *   2. bonds: a_i = s_i . r in FP64; right/down bond <ij> is active iff
+ *             a_i a_j > 0 and u < 1 - exp(-2 beta a_i a_j), u from Philox
+ *             domain BOND of site i (word 0 = right, word 1 = down).
+ *   3. labels: connected components of the active bonds; label = the minimum
+ *             site index of the component (BFS; union-find as a second copy).
+ *   4. flip:  a cluster flips iff word 2 of its root's BOND draw is odd;
+ *             a flipped angle becomes wrap(C32 - theta) in FP32, which is the
+ *             reflection s' = s - 2 (s.r) r of Wolff's embedding.
+ *   5. observables on the flipped configuration: energy, magnetisation and
+ *             the helicity-modulus sums of the paper's Eqs. (4)-(6).
+ *   6. (PCC) beta <- beta + dbeta if beta*Upsilon < target else beta - dbeta
+ *             (the paper's helicity-modulus PCC rule, Sec. 2, after Eq. (6)).
+ *
+ * All floating point is FP64 except where the stored-angle format fixes FP32
+ * (or FP16) arithmetic: the flip and the initial angles.  Built with
+ * -ffp-contract=off and without -ffast-math.
+ */
+#ifndef XY_ORACLE_H
+#define XY_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox counter domains (counter word 3). */
+enum { ORC_DOM_BOND = 0, ORC_DOM_AXIS = 1, ORC_DOM_INIT = 2,
+       ORC_DOM_WORKLOAD = 3, ORC_DOM_METRO = 4 };
+
+/* Observable sums of one configuration (raw, not normalised). */
+typedef struct {
+  double sum_cos;      /* sum_i cos(theta_i)                    */
+  double sum_sin;      /* sum_i sin(theta_i)                    */
+  double sum_cos_r;    /* sum over right links cos(th_i - th_R) */
+  double sum_sin_r;    /* sum over right links sin(th_i - th_R) */
+  double sum_cos_d;    /* sum over down links  cos(th_i - th_D) */
+  double sum_sin_d;    /* sum over down links  sin(th_i - th_D) */
+  double n_sites;      /* N = Lx*Ly                             */
+  double n_links_r;    /* number of right links (N if periodic) */
+  double n_links_d;    /* number of down links                  */
+} orc_sums;
+
+/* Derived per-configuration observables. */
+typedef struct {
+  double energy_per_site;  /* -(sum_cos_r + sum_cos_d) / N                 */
+  double m2;               /* mx^2 + my^2                                  */
+  double mx, my;           /* N^-1 sum cos, N^-1 sum sin                   */
+  double ex, sx;           /* N^-1 sum_x cos, N^-1 sum_x sin (Eqs. 5-6)    */
+  double ey, sy;           /* same along y                                 */
+  double upsilon;          /* ex - beta N sx^2 (Eq. 4, J = 1, T = 1/beta)  */
+  double beta;             /* the beta the configuration was sampled at    */
+} orc_obs;
+
+/* ---- Philox4x32-10 ------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]);
+/* out[4*k + j] = word j of Philox(ctr + k e_word, key(seed)): counter word
+ * `word` (0..3) of ctr advances by k, the other words stay fixed. */
+void orc_philox_stream(uint64_t seed, const uint32_t ctr[4], int word,
+                       uint64_t n_calls, uint32_t *out);
+
+/* ---- one sweep, step by step -------------------------------------------- */
+/* Step 1: axis of sweep t.  out: phi, cos phi, sin phi, C (FP64); c32: C32. */
+void orc_axis(uint64_t seed, uint32_t t, double out[4], float *c32);
+
+/* Initial angles: start 0 = random (domain INIT), 1 = ordered (theta = 0). */
+void orc_init_angles_f32(int Lx, int Ly, uint64_t seed, int start,
+                         float *theta);
+void orc_init_angles_f16(int Lx, int Ly, uint64_t seed, int start,
+                         uint16_t *theta_bits);
+
+/* Step 2: bonds.  right[i], down[i] in {0,1}.  Returns the number of bonds
+ * whose |u - p| < 1e-12 (the reported exception band of exact mode). */
+long orc_bonds_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
+                   double beta, uint64_t seed, uint32_t t, uint8_t *right,
+                   uint8_t *down);
+long orc_bonds_f16(int Lx, int Ly, int per_x, int per_y,
+                   const uint16_t *theta_bits, double beta, uint64_t seed,
+                   uint32_t t, uint8_t *right, uint8_t *down);
+/* Bond probability bookkeeping for a single bond (for the band report):
+ * writes u and p of the right (dir 0) or down (dir 1) bond of site i. */
+void orc_bond_up_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
+                     double beta, uint64_t seed, uint32_t t, int64_t i,
+                     int dir, double *u, double *p);
+
+/* Step 3: labels (minimum site index of each component). Returns the number
+ * of components. */
+long orc_label_bfs(int Lx, int Ly, int per_x, int per_y, const uint8_t *right,
+                   const uint8_t *down, uint32_t *label, uint32_t *queue);
+long orc_label_uf(int Lx, int Ly, int per_x, int per_y, const uint8_t *right,
+                  const uint8_t *down, uint32_t *label);
+
+/* Step 4: flip.  flipped[i] (optional, may be NULL) records the flip set.
+ * Returns the number of flipped sites. */
+long orc_flip_f32(int Lx, int Ly, float *theta, const uint32_t *label,
+                  uint64_t seed, uint32_t t, float c32, uint8_t *flipped);
+long orc_flip_f16(int Lx, int Ly, uint16_t *theta_bits, const uint32_t *label,
+                  uint64_t seed, uint32_t t, float c32, uint8_t *flipped);
+/* coin of a root site: 1 = the cluster is reflected. */
+int orc_coin(uint64_t seed, uint32_t t, uint32_t root);
+
+/* Step 5: observables. */
+void orc_sums_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
+                  orc_sums *s);
+void orc_sums_f16(int Lx, int Ly, int per_x, int per_y,
+                  const uint16_t *theta_bits, orc_sums *s);
+void orc_derive(const orc_sums *s, double beta, orc_obs *o);
+
+/* Step 6: PCC beta update (the paper's helicity-modulus rule).
+ * beta_upsilon: the (block-averaged) beta*Upsilon that drives this step. */
+double orc_pcc_next_beta(double beta, double beta_upsilon, double target,
+                         double dbeta);
+/* dbeta of PCC step k: dbeta0 * 2^-(k / halve_every) (halve_every = 0: fixed). */
+double orc_pcc_dbeta(double dbeta0, uint32_t halve_every, uint32_t k);
+
+/* ---- whole sweeps -------------------------------------------------------- */
+/* Runs n sweeps t0 .. t0+n-1 at fixed beta (FP32 angles), writing one
+ * orc_obs per sweep to obs (may be NULL).  Scratch: right, down (N bytes
+ * each), label and queue (N uint32 each). */
+void orc_sw_run_f32(int Lx, int Ly, int per_x, int per_y, float *theta,
+                    double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                    uint8_t *right, uint8_t *down, uint32_t *label,
+                    uint32_t *queue, orc_obs *obs);
+void orc_sw_run_f16(int Lx, int Ly, int per_x, int per_y,
+                    uint16_t *theta_bits, double beta, uint64_t seed,
+                    uint32_t t0, uint32_t n, uint8_t *right, uint8_t *down,
+                    uint32_t *label, uint32_t *queue, orc_obs *obs);
+
+/* PCC run on a periodic L x L lattice: sweeps t0 .. t0+n-1 (Philox sweep
+ * counter).  k0 is the number of sweeps already run under PCC; the sweep with
+ * PCC index k adds beta_k*Upsilon_k to the block accumulator, and when the
+ * block holds `block` sweeps beta steps by the rule above with
+ * dbeta = orc_pcc_dbeta(dbeta0, halve_every, k), driven by the block mean.
+ * beta, blk_acc and blk_count are updated in place; obs records the beta each
+ * sweep ran at. */
+void orc_pcc_run_f32(int L, float *theta, double *beta, double target,
+                     double dbeta0, uint32_t halve_every, uint32_t block,
+                     uint64_t seed, uint32_t t0, uint32_t k0, uint32_t n,
+                     double *blk_acc, uint32_t *blk_count, uint8_t *right,
+                     uint8_t *down, uint32_t *label, uint32_t *queue,
+                     orc_obs *obs);
+
+/* Metropolis single-spin-flip sweeps (typewriter order, FP64 angles), an
+ * independent sampler used only to cross-check the cluster chain. */
+void orc_metropolis_run(int Lx, int Ly, double *theta, double beta,
+                        double delta, uint64_t seed, uint32_t t0, uint32_t n,
+                        orc_obs *obs, long *accepted);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
