@@ -1,0 +1,219 @@
+/*
+ * xy.h -- C ABI of the B300 (sm_103a) Swendsen-Wang sweep for the 2D
+ * classical XY model with Wolff's embedded-Ising reflection.
+ *
+ * The model is the paper's Eq. (3): H = -J sum_<ij> cos(theta_i - theta_j),
+ * J = 1, nearest neighbours of an L x L square lattice with periodic
+ * boundaries (Komura & Okabe, Sec. 2).  One sweep (one MCS, Sec. 3) is the
+ * Swendsen-Wang multi-cluster update (Sec. 1) in Wolff's embedding:
+ *   1. draw a random unit vector r = (cos phi, sin phi);
+ *   2. activate each nearest-neighbour bond with probability
+ *      p = 1 - exp(-2 beta (s_i.r)(s_j.r)) where that product is positive;
+ *   3. label the connected clusters (label = minimum site index);
+ *   4. reflect each cluster about r (s -> s - 2 (s.r) r) with probability 1/2;
+ *   5. accumulate energy, M^2 and the helicity-modulus sums (Eqs. (4)-(6)).
+ * The helicity-modulus PCC (Sec. 2, after Eq. (6)) steps beta after each
+ * sweep or block of sweeps: up if beta*Upsilon is below the target, down
+ * otherwise.
+ *
+ * Conventions
+ *   - Every call returns an xy_status; xy_last_error() gives a message for
+ *     the calling thread.  No C++ exception crosses this boundary.
+ *   - Ownership: the CALLER owns all device memory (one workspace buffer per
+ *     lattice, sized by xy_workspace_size) and the CUDA stream.  The library
+ *     owns only the small opaque host handle; xy_destroy frees the handle and
+ *     never the caller's buffers.
+ *   - All calls are asynchronous on the handle's stream, except the host-copy
+ *     getters/setters and xy_measure with sync = 1, which synchronise it.
+ *   - Site index i = y * L + x (row-major, x fastest).  Angles live in
+ *     [0, 2 pi) radians, stored as FP32 or IEEE FP16.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed
+ *     (low word, high word) and counter (site, 0, sweep, domain); every bit of
+ *     a sweep is a pure function of (seed, sweep, site), so results do not
+ *     depend on launch shapes, batching or reduction order.
+ *   - Device-side failures (a bounded wait that ran out) never trap: the
+ *     kernel records an error word, finishes its launch and the next
+ *     synchronising call returns XY_ETIMEOUT or XY_EINTERNAL.
+ */
+#ifndef XY_H
+#define XY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XY_OK = 0,
+  XY_EINVAL = 1,       /* bad argument; nothing was launched            */
+  XY_ENOMEM = 2,       /* workspace or host buffer too small            */
+  XY_ECUDA = 3,        /* a CUDA runtime call failed                    */
+  XY_ETIMEOUT = 4,     /* a bounded device-side loop hit its limit      */
+  XY_EINTERNAL = 5,    /* a device-side consistency check failed        */
+  XY_EUNSUPPORTED = 6  /* valid request this build does not implement   */
+} xy_status;
+
+typedef struct xy_lattice xy_lattice; /* opaque host handle */
+
+typedef enum { XY_F32 = 0, XY_F16 = 1 } xy_angle_t;
+
+/* Bond-threshold arithmetic.  XY_THR_F64 ("exact mode") decides every bond as
+ * the FP64 rule u < 1 - exp(-2 beta a_i a_j) does: an FP32 evaluation with a
+ * proven error bound settles all bonds outside a narrow band, and the bonds
+ * inside it are recomputed in FP64.  XY_THR_F32 uses the FP32 evaluation
+ * alone (faster, differs from the FP64 rule on a measured small fraction of
+ * bonds). */
+typedef enum { XY_THR_F32 = 0, XY_THR_F64 = 1 } xy_thr_t;
+
+typedef struct {
+  uint32_t L;              /* linear size, 2 .. 65536 (N = L*L <= 2^32)     */
+  uint32_t tile_y;         /* labeling tile height: 16, 32, 64 or 128;
+                              0 = the library's choice for this L          */
+  uint64_t seed;           /* Philox key                                    */
+  double beta;             /* inverse temperature J/T, >= 0                 */
+  int32_t angle_dtype;     /* xy_angle_t                                    */
+  int32_t threshold_mode;  /* xy_thr_t                                      */
+  int32_t start;           /* 0: random angles (Philox domain INIT),
+                              1: ordered start (all angles 0)               */
+  uint32_t record_cap;     /* observable records kept on the device (ring);
+                              0 = 4096                                      */
+} xy_config;
+
+/* Observables of the configuration after one sweep (FP64).  N = L*L.
+ *   energy_per_site = -(sum_x cos + sum_y cos)/N            (Eq. (3) / N)
+ *   mx, my = N^-1 sum (cos theta, sin theta); m2 = mx^2 + my^2
+ *   ex, sx = N^-1 sum over x-links of cos, sin (theta_i - theta_{i+x})
+ *                                                           (Eqs. (5), (6))
+ *   ey, sy = the same over y-links
+ *   upsilon = ex - beta N sx^2   (Eq. (4) with J = 1, T = 1/beta, L^2 = N);
+ *             the paper's PCC compares beta*upsilon with its target
+ *   beta   = the inverse temperature the sweep ran at
+ *   sweep  = the sweep counter t of that sweep (0-based)                  */
+typedef struct {
+  double energy_per_site, m2, mx, my, ex, sx, ey, sy, upsilon, beta;
+  uint64_t sweep;
+} xy_obs;
+
+/* Helicity-modulus PCC (Sec. 2): after every `block` sweeps, with
+ * m = mean of beta_t*upsilon_t over the block,
+ *   beta <- beta + dbeta  if m <  target
+ *   beta <- beta - dbeta  otherwise (ties decrease),
+ * dbeta = dbeta0 * 2^-floor(k / halve_every) (halve_every = 0: constant),
+ * k = the PCC sweep index of the block's last sweep (sweeps run under PCC
+ * since xy_init).  The paper's protocol: target 0.636508, dbeta0 0.0005,
+ * halve_every 0, block 1000 (Sec. 3). */
+typedef struct {
+  double target;
+  double dbeta0;
+  uint32_t halve_every;
+  uint32_t block;
+} xy_pcc_params;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *xy_last_error(void);
+
+/* Bytes of device workspace a lattice with this config needs.  The layout is
+ * private; the caller provides one buffer of at least this size, 256-byte
+ * aligned (any cudaMalloc / torch allocation is).  XY_EINVAL on a bad
+ * config. */
+xy_status xy_workspace_size(const xy_config *cfg, size_t *bytes);
+
+/* Create a lattice in the caller's workspace and enqueue its initialisation
+ * on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * XY_EINVAL: bad config, NULL pointers or misaligned workspace;
+ * XY_ENOMEM: `bytes` below xy_workspace_size.  The workspace must stay
+ * allocated until xy_destroy. */
+xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
+                  void *cuda_stream, xy_lattice **out);
+
+/* Enqueue n_sweeps sweeps at the current beta.  Each sweep appends one
+ * xy_obs record to the device ring.  Asynchronous. */
+xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps);
+
+/* Enqueue n_sweeps PCC sweeps: each sweep is followed by the PCC rule above.
+ * beta lives on the device, so no host round trip happens between sweeps.
+ * XY_EINVAL on NULL params, block = 0, or negative dbeta0. */
+xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p,
+                      uint32_t n_sweeps);
+
+/* Copy the records of the sweeps enqueued since the previous xy_measure
+ * call into `out` (chronological order).  If more than max_records (or
+ * more than the ring capacity) are pending, only the newest ones are
+ * returned; *n_out receives the number written.  sync = 1 synchronises the
+ * stream first and reports any device-side error (XY_ETIMEOUT /
+ * XY_EINTERNAL); sync = 0 skips both, so the caller must have synchronised
+ * the stream itself. */
+xy_status xy_measure(xy_lattice *h, xy_obs *out, uint32_t max_records,
+                     uint32_t *n_out, int sync);
+
+/* Current beta and sweep counter (synchronising). */
+xy_status xy_get_state(xy_lattice *h, double *beta, uint64_t *sweep);
+
+/* Destroy the handle (never frees the caller's workspace). */
+xy_status xy_destroy(xy_lattice *h);
+
+/* ---- host copies (synchronising) --------------------------------------- */
+/* Angles: N elements of the lattice dtype (float or IEEE half bits), row-
+ * major.  Set values must lie in [0, 2 pi); XY_EINVAL otherwise. */
+xy_status xy_get_angles(xy_lattice *h, void *host_dst);
+xy_status xy_set_angles(xy_lattice *h, const void *host_src);
+/* Bonds of the last sweep as N bytes each (1 = active): right[i] is the bond
+ * (x, y)-(x+1 mod L, y), down[i] the bond (x, y)-(x, y+1 mod L). */
+xy_status xy_get_bonds(xy_lattice *h, uint8_t *host_right,
+                       uint8_t *host_down);
+/* Cluster labels of the last sweep: N uint32, label = minimum site index of
+ * the cluster. */
+xy_status xy_get_labels(xy_lattice *h, uint32_t *host_dst);
+/* Label caller-supplied bond bytes (N each, same meaning as xy_get_bonds)
+ * with the device labeling kernels; writes N labels.  Does not touch the
+ * angles, the sweep counter or the records. */
+xy_status xy_label_bonds(xy_lattice *h, const uint8_t *host_right,
+                         const uint8_t *host_down, uint32_t *host_labels);
+/* Diagnostics of exact mode since xy_init: bonds decided in FP64 (inside
+ * the FP32 error band) and, among them, those where the FP32 decision would
+ * have differed. */
+xy_status xy_get_band_stats(xy_lattice *h, uint64_t *n_fp64,
+                            uint64_t *n_fp32_wrong);
+
+/* ---- host-buffer run (end to end) -------------------------------------- */
+/* One call that does what a caller with host data does: copy N angles in
+ * from host memory (skipped when host_angles_in is NULL), run n_sweeps
+ * sweeps, copy the n_sweeps observable records out to host_obs (may be NULL)
+ * and the final N angles out to host_angles_out (may be NULL), then
+ * synchronise.  Pinned host buffers make the copies asynchronous DMA; the
+ * input angles are not range-checked here (values outside [0, 2 pi) give
+ * meaningless observables but no fault).  Device-side errors are reported as
+ * by xy_measure(sync = 1).  Records returned here are not returned again by
+ * xy_measure. */
+xy_status xy_run_host(xy_lattice *h, const void *host_angles_in,
+                      uint32_t n_sweeps, xy_obs *host_obs,
+                      void *host_angles_out);
+
+/* ---- kernel timing ------------------------------------------------------- */
+/* Kernel index of xy_kernel_times: 0 bond+tile label, 1 edge merge,
+ * 2 compress, 3 flip+measure, 4 finalize. */
+#define XY_NUM_KERNELS 5
+typedef struct {
+  double ms[XY_NUM_KERNELS];          /* summed device time (CUDA events)  */
+  uint64_t launches[XY_NUM_KERNELS];  /* launches timed                    */
+} xy_kernel_times;
+/* enable = 1: from now on bracket every kernel of every sweep with CUDA
+ * events on the lattice's stream (resets the totals); enable = 0: stop. */
+xy_status xy_profile(xy_lattice *h, int enable);
+/* Synchronise and return the totals since profiling was enabled. */
+xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out);
+
+/* ---- checkpoint --------------------------------------------------------- */
+/* Serialise the full chain state (angles, seed, sweep counter, beta, PCC
+ * accumulators, dtype) into host memory.  Call with blob = NULL to get the
+ * size in *bytes.  Resuming from a checkpoint reproduces the uninterrupted
+ * run bit for bit (the random numbers are a function of the sweep counter). */
+xy_status xy_save(xy_lattice *h, void *host_blob, size_t *bytes);
+xy_status xy_load(xy_lattice *h, const void *host_blob, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XY_H */

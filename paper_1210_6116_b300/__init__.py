@@ -1,0 +1,291 @@
+"""B300 (sm_103a) Swendsen-Wang sweep of the 2D classical XY model.
+
+Thin ctypes binding of the C ABI in ``include/xy.h`` (libxy.so, built
+in-tree).  Every step of a sweep runs in the library's CUDA kernels; this
+module only marshals arguments.  PyTorch provides the device workspace and the
+stream.  There is no CPU fallback: importing the package on a machine where
+libxy.so cannot be loaded raises.
+
+Functions with the C names (``xy_init``, ``xy_sweep``, ``xy_measure``,
+``xy_pcc_step`` ...) mirror the ABI one to one; ``Lattice`` bundles a handle
+with its workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libxy.so"
+
+XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_EINTERNAL, XY_EUNSUPPORTED = range(7)
+XY_F32, XY_F16 = 0, 1
+XY_THR_F32, XY_THR_F64 = 0, 1
+
+STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "XY_ETIMEOUT",
+                5: "XY_EINTERNAL", 6: "XY_EUNSUPPORTED"}
+
+# every entry point declared in include/xy.h
+EXPORTS = (
+    "xy_last_error", "xy_workspace_size", "xy_init", "xy_sweep", "xy_pcc_step",
+    "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
+    "xy_get_bonds", "xy_get_labels", "xy_label_bonds", "xy_get_band_stats", "xy_save",
+    "xy_load", "xy_run_host", "xy_profile", "xy_profile_read",
+)
+KERNEL_NAMES = ("bond_label", "merge", "compress", "flip_measure", "finalize")
+
+
+class XyError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class xy_config(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint32), ("tile_y", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("beta", ctypes.c_double), ("angle_dtype", ctypes.c_int32),
+                ("threshold_mode", ctypes.c_int32), ("start", ctypes.c_int32),
+                ("record_cap", ctypes.c_uint32)]
+
+
+OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy", "upsilon", "beta")
+
+
+class xy_obs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in OBS_FIELDS] + [("sweep", ctypes.c_uint64)]
+
+
+OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS] + [("sweep", np.uint64)])
+assert OBS_DTYPE.itemsize == ctypes.sizeof(xy_obs)
+
+
+class xy_kernel_times(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_uint64 * 5)]
+
+
+class xy_pcc_params(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_double), ("dbeta0", ctypes.c_double),
+                ("halve_every", ctypes.c_uint32), ("block", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libxy.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                           "`python -m paper_1210_6116_b300.build`")
+    L = ctypes.CDLL(str(LIB_PATH))
+    P, U32, U64, I, D = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    sigs = {
+        "xy_last_error": (ctypes.c_char_p, []),
+        "xy_workspace_size": (I, [P, P]),
+        "xy_init": (I, [P, P, ctypes.c_size_t, P, P]),
+        "xy_sweep": (I, [P, U32]),
+        "xy_pcc_step": (I, [P, P, U32]),
+        "xy_measure": (I, [P, P, U32, P, I]),
+        "xy_get_state": (I, [P, P, P]),
+        "xy_destroy": (I, [P]),
+        "xy_get_angles": (I, [P, P]),
+        "xy_set_angles": (I, [P, P]),
+        "xy_get_bonds": (I, [P, P, P]),
+        "xy_get_labels": (I, [P, P]),
+        "xy_label_bonds": (I, [P, P, P, P]),
+        "xy_get_band_stats": (I, [P, P, P]),
+        "xy_save": (I, [P, P, P]),
+        "xy_load": (I, [P, P, ctypes.c_size_t]),
+        "xy_run_host": (I, [P, P, U32, P, P]),
+        "xy_profile": (I, [P, I]),
+        "xy_profile_read": (I, [P, P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != XY_OK:
+        raise XyError(status, load_library().xy_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def xy_workspace_size(cfg: xy_config) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().xy_workspace_size(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def xy_init(cfg: xy_config, d_workspace: int, nbytes: int, stream: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().xy_init(ctypes.byref(cfg), ctypes.c_void_p(d_workspace), nbytes,
+                                  ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def xy_sweep(h, n: int):
+    _check(load_library().xy_sweep(h, n))
+
+
+def xy_pcc_step(h, params: xy_pcc_params, n: int):
+    _check(load_library().xy_pcc_step(h, ctypes.byref(params), n))
+
+
+def xy_measure(h, max_records: int, sync: int = 1) -> np.ndarray:
+    out = np.zeros(max_records, OBS_DTYPE)
+    n = ctypes.c_uint32(0)
+    _check(load_library().xy_measure(h, _ptr(out) if max_records else None, max_records,
+                                     ctypes.byref(n), sync))
+    return out[: n.value]
+
+
+def xy_get_state(h):
+    b = ctypes.c_double(0)
+    t = ctypes.c_uint64(0)
+    _check(load_library().xy_get_state(h, ctypes.byref(b), ctypes.byref(t)))
+    return b.value, t.value
+
+
+def xy_destroy(h):
+    _check(load_library().xy_destroy(h))
+
+
+def xy_last_error() -> str:
+    return load_library().xy_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# Lattice: a handle plus its torch-owned workspace
+# ---------------------------------------------------------------------------
+class Lattice:
+    """One L x L periodic lattice resident in device memory.
+
+    The workspace is a torch uint8 tensor on the current CUDA device; all
+    launches go to ``stream`` (default: torch's current stream)."""
+
+    def __init__(self, L: int, beta: float, seed: int, *, dtype: str = "f32",
+                 exact: bool = True, start: str = "random", tile_y: int = 0,
+                 record_cap: int = 0, stream=None):
+        import torch  # plumbing: device memory and streams
+
+        self.L = int(L)
+        self.dtype = dtype
+        self.np_dtype = np.float32 if dtype == "f32" else np.float16
+        self.cfg = xy_config(L=self.L, tile_y=tile_y, seed=seed, beta=beta,
+                             angle_dtype=XY_F32 if dtype == "f32" else XY_F16,
+                             threshold_mode=XY_THR_F64 if exact else XY_THR_F32,
+                             start=0 if start == "random" else 1, record_cap=record_cap)
+        self.nbytes = xy_workspace_size(self.cfg)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.handle = xy_init(self.cfg, self.workspace.data_ptr(), self.nbytes,
+                              self.stream.cuda_stream)
+
+    # -- chain ---------------------------------------------------------------
+    def sweep(self, n: int = 1):
+        xy_sweep(self.handle, n)
+
+    def pcc_step(self, n: int, target: float = 0.636508, dbeta0: float = 0.0005,
+                 halve_every: int = 0, block: int = 1000):
+        xy_pcc_step(self.handle, xy_pcc_params(target=target, dbeta0=dbeta0,
+                                               halve_every=halve_every, block=block), n)
+
+    def measure(self, max_records: int = 1 << 20, sync: bool = True) -> np.ndarray:
+        return xy_measure(self.handle, max_records, 1 if sync else 0)
+
+    def state(self):
+        return xy_get_state(self.handle)
+
+    # -- host copies ---------------------------------------------------------
+    @property
+    def n(self) -> int:
+        return self.L * self.L
+
+    def get_angles(self) -> np.ndarray:
+        out = np.zeros(self.n, self.np_dtype)
+        _check(load_library().xy_get_angles(self.handle, _ptr(out)))
+        return out
+
+    def set_angles(self, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=self.np_dtype)
+        assert a.size == self.n
+        _check(load_library().xy_set_angles(self.handle, _ptr(a)))
+
+    def get_bonds(self):
+        r = np.zeros(self.n, np.uint8)
+        d = np.zeros(self.n, np.uint8)
+        _check(load_library().xy_get_bonds(self.handle, _ptr(r), _ptr(d)))
+        return r, d
+
+    def get_labels(self) -> np.ndarray:
+        out = np.zeros(self.n, np.uint32)
+        _check(load_library().xy_get_labels(self.handle, _ptr(out)))
+        return out
+
+    def label_bonds(self, right: np.ndarray, down: np.ndarray) -> np.ndarray:
+        r = np.ascontiguousarray(right, np.uint8)
+        d = np.ascontiguousarray(down, np.uint8)
+        out = np.zeros(self.n, np.uint32)
+        _check(load_library().xy_label_bonds(self.handle, _ptr(r), _ptr(d), _ptr(out)))
+        return out
+
+    def band_stats(self):
+        a = ctypes.c_uint64(0)
+        b = ctypes.c_uint64(0)
+        _check(load_library().xy_get_band_stats(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def run_host(self, angles_in, n_sweeps: int, obs_out=None, angles_out=None):
+        """xy_run_host with numpy (optionally pinned) host buffers."""
+        pin = (lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data))
+        _check(load_library().xy_run_host(self.handle, pin(angles_in), n_sweeps,
+                                          pin(obs_out), pin(angles_out)))
+
+    def profile(self, enable: bool):
+        _check(load_library().xy_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        t = xy_kernel_times()
+        _check(load_library().xy_profile_read(self.handle, ctypes.byref(t)))
+        return {name: (t.ms[k], int(t.launches[k])) for k, name in enumerate(KERNEL_NAMES)}
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(load_library().xy_save(self.handle, None, ctypes.byref(n)))
+        buf = (ctypes.c_char * n.value)()
+        _check(load_library().xy_save(self.handle, buf, ctypes.byref(n)))
+        return bytes(buf)
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(load_library().xy_load(self.handle, buf, len(blob)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            xy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+TWO_PI_F32 = np.float32(2.0 * math.pi)

@@ -1,0 +1,642 @@
+// xy_api.cu -- host side of the C ABI declared in include/xy.h.
+//
+// The library owns only the small host handle; every device byte lives in the
+// caller's workspace.  A sweep is five stream-ordered launches (bond+tile
+// label, merge, compress, flip+measure, finalize) that read all per-sweep
+// parameters (sweep counter, beta, axis) from device state, so a sequence of
+// sweeps needs no host round trip and can be captured in a CUDA graph.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/xy.h"
+#include "sweep_kernels.cuh"
+
+using namespace xyk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+xy_status fail(xy_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define XY_CUDA(call)                                                       \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return fail(XY_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+uint32_t default_tile_y(uint32_t L) {
+  if (L <= 32) return 16;
+  if (L <= 256) return 32;
+  return 64;
+}
+
+bool tile_ok(uint32_t ty) { return ty == 16 || ty == 32 || ty == 64 || ty == 128; }
+
+struct Layout {
+  uint32_t L, TY, ntx, nty, ntiles, rec_cap;
+  size_t esize;
+  size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0,
+      off_theta1, off_label, off_rplane, off_dplane, off_coin, total;
+};
+
+xy_status make_layout(const xy_config *c, Layout *lo) {
+  if (!c) return fail(XY_EINVAL, "config is NULL");
+  if (c->L < 2 || c->L > 65536)
+    return fail(XY_EINVAL, "L = %u outside 2..65536", c->L);
+  if (!(c->beta >= 0.0) || !std::isfinite(c->beta))
+    return fail(XY_EINVAL, "beta must be finite and >= 0");
+  if (c->angle_dtype != XY_F32 && c->angle_dtype != XY_F16)
+    return fail(XY_EINVAL, "angle_dtype must be XY_F32 or XY_F16");
+  if (c->threshold_mode != XY_THR_F32 && c->threshold_mode != XY_THR_F64)
+    return fail(XY_EINVAL, "threshold_mode must be XY_THR_F32 or XY_THR_F64");
+  if (c->start != 0 && c->start != 1)
+    return fail(XY_EINVAL, "start must be 0 (random) or 1 (ordered)");
+  const uint32_t ty = c->tile_y ? c->tile_y : default_tile_y(c->L);
+  if (!tile_ok(ty)) return fail(XY_EINVAL, "tile_y must be 16, 32, 64 or 128");
+  lo->L = c->L;
+  lo->TY = ty;
+  lo->ntx = (c->L + 31) / 32;
+  lo->nty = (c->L + ty - 1) / ty;
+  lo->ntiles = lo->ntx * lo->nty;
+  lo->rec_cap = c->record_cap ? c->record_cap : 4096;
+  lo->esize = c->angle_dtype == XY_F32 ? 4 : 2;
+  const uint64_t n = static_cast<uint64_t>(c->L) * c->L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  lo->off_state = take(sizeof(DevState));
+  lo->off_desc = take(sizeof(LatDesc));
+  lo->off_prefix = take(2 * sizeof(uint32_t));
+  lo->off_acc = take(sizeof(long long) * kSlots * kAccStride);
+  lo->off_rec = take(sizeof(ObsRecord) * lo->rec_cap);
+  lo->off_theta0 = take(n * lo->esize);
+  lo->off_theta1 = take(n * lo->esize);
+  lo->off_label = take(n * sizeof(uint32_t));
+  lo->off_rplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
+  lo->off_dplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
+  lo->off_coin = take((n / 32 + 2) * sizeof(uint32_t));
+  lo->total = off;
+  return XY_OK;
+}
+
+}  // namespace
+
+struct xy_lattice {
+  xy_config cfg;
+  Layout lo;
+  cudaStream_t stream;
+  char *ws;
+  LatDesc desc;       // host copy of the device descriptor
+  LatDesc *d_desc;
+  uint32_t *d_prefix;
+  DevState *d_state;
+  uint64_t enqueued;  // sweeps enqueued since xy_init
+  uint64_t reported;  // sweeps already returned by xy_measure
+  int sm_count;
+  // kernel timing: 6 events per sweep bracket its 5 kernels
+  bool prof;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used;
+};
+
+namespace {
+
+// records the next timing event of a profiled sweep (no-op otherwise)
+cudaError_t mark(xy_lattice *h) {
+  if (!h->prof) return cudaSuccess;
+  if (h->ev_used == h->events.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    h->events.push_back(e);
+  }
+  return cudaEventRecord(h->events[h->ev_used++], h->stream);
+}
+
+template <int TY, typename AT, bool EXACT>
+cudaError_t launch_sweep_t(xy_lattice *h) {
+  const uint32_t nw = h->lo.ntiles;
+  cudaStream_t s = h->stream;
+  cudaError_t e;
+  if (h->desc.ragged) {
+    e = cudaMemsetAsync(h->desc.coin, 0, (static_cast<size_t>(h->lo.L) * h->lo.L / 32 + 2) * 4, s);
+    if (e != cudaSuccess) return e;
+  }
+  if ((e = mark(h)) != cudaSuccess) return e;
+  k_bond_label<TY, AT, EXACT, false>
+      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if ((e = mark(h)) != cudaSuccess) return e;
+  const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if ((e = mark(h)) != cudaSuccess) return e;
+  k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if ((e = mark(h)) != cudaSuccess) return e;
+  k_flip_measure<TY, AT, false>
+      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if ((e = mark(h)) != cudaSuccess) return e;
+  k_finalize<<<1, 32, 0, s>>>(h->d_desc, 1);
+  if ((e = mark(h)) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int TY, typename AT, bool EXACT>
+cudaError_t set_attrs_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(bond_label_smem<TY>()));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(bond_label_smem<TY>()));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_flip_measure<TY, AT, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(flip_smem<TY>()));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_flip_measure<TY, AT, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(flip_smem<TY>()));
+}
+
+template <int TY, typename AT>
+cudaError_t dispatch_exact(xy_lattice *h, bool attrs) {
+  if (h->cfg.threshold_mode == XY_THR_F64)
+    return attrs ? set_attrs_t<TY, AT, true>() : launch_sweep_t<TY, AT, true>(h);
+  return attrs ? set_attrs_t<TY, AT, false>() : launch_sweep_t<TY, AT, false>(h);
+}
+
+template <typename AT>
+cudaError_t dispatch_ty(xy_lattice *h, bool attrs) {
+  switch (h->lo.TY) {
+    case 16: return dispatch_exact<16, AT>(h, attrs);
+    case 32: return dispatch_exact<32, AT>(h, attrs);
+    case 64: return dispatch_exact<64, AT>(h, attrs);
+    default: return dispatch_exact<128, AT>(h, attrs);
+  }
+}
+
+cudaError_t launch_sweep(xy_lattice *h) {
+  return h->cfg.angle_dtype == XY_F32 ? dispatch_ty<float>(h, false)
+                                      : dispatch_ty<__half>(h, false);
+}
+
+cudaError_t set_attrs(xy_lattice *h) {
+  return h->cfg.angle_dtype == XY_F32 ? dispatch_ty<float>(h, true)
+                                      : dispatch_ty<__half>(h, true);
+}
+
+// labeling only, from the bond planes already in the workspace
+template <int TY>
+cudaError_t launch_label_only_t(xy_lattice *h) {
+  const uint32_t nw = h->lo.ntiles;
+  cudaStream_t s = h->stream;
+  k_bond_label<TY, float, true, true>
+      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  k_flip_measure<TY, float, true>
+      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_only(xy_lattice *h) {
+  if (h->cfg.angle_dtype != XY_F32) {
+    // the label-only kernels are dtype-agnostic; make sure their attributes
+    // are set even when the lattice itself is FP16
+    cudaError_t e;
+    switch (h->lo.TY) {
+      case 16: e = set_attrs_t<16, float, true>(); break;
+      case 32: e = set_attrs_t<32, float, true>(); break;
+      case 64: e = set_attrs_t<64, float, true>(); break;
+      default: e = set_attrs_t<128, float, true>(); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  switch (h->lo.TY) {
+    case 16: return launch_label_only_t<16>(h);
+    case 32: return launch_label_only_t<32>(h);
+    case 64: return launch_label_only_t<64>(h);
+    default: return launch_label_only_t<128>(h);
+  }
+}
+
+xy_status check_device_error(xy_lattice *h) {
+  uint32_t err = 0;
+  XY_CUDA(cudaMemcpy(&err, &h->d_state->err, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err & (kErrFindCap | kErrUnionCap))
+    return fail(XY_ETIMEOUT, "device-side find/union loop hit its bound (err=%#x)", err);
+  if (err) return fail(XY_EINTERNAL, "device error word %#x", err);
+  return XY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *xy_last_error(void) { return g_err; }
+
+xy_status xy_workspace_size(const xy_config *cfg, size_t *bytes) {
+  if (!bytes) return fail(XY_EINVAL, "bytes is NULL");
+  Layout lo;
+  xy_status s = make_layout(cfg, &lo);
+  if (s != XY_OK) return s;
+  *bytes = lo.total;
+  return XY_OK;
+}
+
+xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
+                  void *cuda_stream, xy_lattice **out) {
+  if (!out) return fail(XY_EINVAL, "out is NULL");
+  *out = nullptr;
+  Layout lo;
+  xy_status st = make_layout(cfg, &lo);
+  if (st != XY_OK) return st;
+  if (!d_workspace) return fail(XY_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256)
+    return fail(XY_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < lo.total)
+    return fail(XY_ENOMEM, "workspace of %zu bytes, %zu needed", bytes, lo.total);
+  xy_lattice *h = new (std::nothrow) xy_lattice();
+  if (!h) return fail(XY_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  h->lo = lo;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->ws = static_cast<char *>(d_workspace);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete h;
+    return fail(XY_ECUDA, "no CUDA device");
+  }
+  LatDesc &d = h->desc;
+  d.L = lo.L;
+  d.ntx = lo.ntx;
+  d.nty = lo.nty;
+  d.ntiles = lo.ntiles;
+  d.key0 = static_cast<uint32_t>(cfg->seed & 0xFFFFFFFFu);
+  d.key1 = static_cast<uint32_t>(cfg->seed >> 32);
+  d.rec_cap = lo.rec_cap;
+  d.ragged = (lo.L % 32) != 0;
+  d.theta[0] = h->ws + lo.off_theta0;
+  d.theta[1] = h->ws + lo.off_theta1;
+  d.label = reinterpret_cast<uint32_t *>(h->ws + lo.off_label);
+  d.rplane = reinterpret_cast<uint32_t *>(h->ws + lo.off_rplane);
+  d.dplane = reinterpret_cast<uint32_t *>(h->ws + lo.off_dplane);
+  d.coin = reinterpret_cast<uint32_t *>(h->ws + lo.off_coin);
+  d.acc = reinterpret_cast<long long *>(h->ws + lo.off_acc);
+  d.st = reinterpret_cast<DevState *>(h->ws + lo.off_state);
+  d.rec = reinterpret_cast<ObsRecord *>(h->ws + lo.off_rec);
+  h->d_desc = reinterpret_cast<LatDesc *>(h->ws + lo.off_desc);
+  h->d_prefix = reinterpret_cast<uint32_t *>(h->ws + lo.off_prefix);
+  h->d_state = d.st;
+  const uint32_t prefix[2] = {0u, lo.ntiles};
+  auto bail = [&](const char *what, cudaError_t e) {
+    delete h;
+    return fail(XY_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = set_attrs(h)) != cudaSuccess) return bail("cudaFuncSetAttribute", e);
+  if ((e = cudaMemcpyAsync(h->d_desc, &h->desc, sizeof(LatDesc), cudaMemcpyHostToDevice,
+                           h->stream)) != cudaSuccess)
+    return bail("descriptor upload", e);
+  if ((e = cudaMemcpyAsync(h->d_prefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice,
+                           h->stream)) != cudaSuccess)
+    return bail("prefix upload", e);
+  if ((e = cudaMemsetAsync(d.acc, 0, sizeof(long long) * kSlots * kAccStride, h->stream)) !=
+      cudaSuccess)
+    return bail("accumulator reset", e);
+  if ((e = cudaMemsetAsync(d.coin, 0, (static_cast<size_t>(lo.L) * lo.L / 32 + 2) * 4,
+                           h->stream)) != cudaSuccess)
+    return bail("coin reset", e);
+  k_init_state<<<1, 1, 0, h->stream>>>(d, cfg->beta);
+  const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;
+  const uint32_t blocks = static_cast<uint32_t>(
+      std::min<uint64_t>((n + 255) / 256, static_cast<uint64_t>(h->sm_count) * 16));
+  if (cfg->angle_dtype == XY_F32)
+    k_init_angles<float><<<blocks, 256, 0, h->stream>>>(d, cfg->start);
+  else
+    k_init_angles<__half><<<blocks, 256, 0, h->stream>>>(d, cfg->start);
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail("init launch", e);
+  // the host copies above read stack memory: finish them before returning
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail("init sync", e);
+  *out = h;
+  return XY_OK;
+}
+
+xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 0u, 0.0, 0.0, 0u, 1u);
+  for (uint32_t k = 0; k < n_sweeps; ++k) XY_CUDA(launch_sweep(h));
+  XY_CUDA(cudaGetLastError());
+  h->enqueued += n_sweeps;
+  return XY_OK;
+}
+
+xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p, uint32_t n_sweeps) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  if (!p) return fail(XY_EINVAL, "params is NULL");
+  if (p->block == 0) return fail(XY_EINVAL, "block must be >= 1");
+  if (!(p->dbeta0 >= 0.0) || !std::isfinite(p->dbeta0) || !std::isfinite(p->target))
+    return fail(XY_EINVAL, "dbeta0 must be finite and >= 0, target finite");
+  k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 1u, p->target, p->dbeta0, p->halve_every,
+                                    p->block);
+  for (uint32_t k = 0; k < n_sweeps; ++k) XY_CUDA(launch_sweep(h));
+  XY_CUDA(cudaGetLastError());
+  h->enqueued += n_sweeps;
+  return XY_OK;
+}
+
+xy_status xy_measure(xy_lattice *h, xy_obs *out, uint32_t max_records, uint32_t *n_out,
+                     int sync) {
+  if (!h || !n_out) return fail(XY_EINVAL, "NULL argument");
+  *n_out = 0;
+  if (max_records && !out) return fail(XY_EINVAL, "out is NULL");
+  if (sync) {
+    XY_CUDA(cudaStreamSynchronize(h->stream));
+    xy_status s = check_device_error(h);
+    if (s != XY_OK) return s;
+  }
+  const uint64_t pending = h->enqueued - h->reported;
+  const uint64_t avail = std::min<uint64_t>(pending, h->lo.rec_cap);
+  const uint64_t take = std::min<uint64_t>(avail, max_records);
+  const uint64_t first = h->enqueued - take;  // sweep index of the first record returned
+  for (uint64_t k = 0; k < take;) {
+    const uint64_t slot = (first + k) % h->lo.rec_cap;
+    const uint64_t run = std::min<uint64_t>(take - k, h->lo.rec_cap - slot);
+    XY_CUDA(cudaMemcpy(out + k, h->desc.rec + slot, run * sizeof(xy_obs),
+                       cudaMemcpyDeviceToHost));
+    k += run;
+  }
+  h->reported = h->enqueued;
+  *n_out = static_cast<uint32_t>(take);
+  return XY_OK;
+}
+
+xy_status xy_get_state(xy_lattice *h, double *beta, uint64_t *sweep) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  DevState s;
+  XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
+  if (beta) *beta = s.beta;
+  if (sweep) *sweep = s.t;
+  return XY_OK;
+}
+
+xy_status xy_destroy(xy_lattice *h) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  delete h;
+  return XY_OK;
+}
+
+xy_status xy_run_host(xy_lattice *h, const void *host_angles_in, uint32_t n_sweeps,
+                      xy_obs *host_obs, void *host_angles_out) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  const size_t ab = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
+  // the angle buffer the next sweep reads is theta[cur]; cur flips once per
+  // sweep, so it is known on the host from the number of sweeps enqueued
+  const uint32_t cur0 = static_cast<uint32_t>(h->enqueued & 1u);
+  if (host_angles_in)
+    XY_CUDA(cudaMemcpyAsync(h->desc.theta[cur0], host_angles_in, ab, cudaMemcpyHostToDevice,
+                            h->stream));
+  xy_status s = xy_sweep(h, n_sweeps);
+  if (s != XY_OK) return s;
+  const uint32_t cur1 = static_cast<uint32_t>(h->enqueued & 1u);
+  if (host_obs && n_sweeps) {
+    const uint64_t take = std::min<uint64_t>(n_sweeps, h->lo.rec_cap);
+    const uint64_t first = h->enqueued - take;
+    for (uint64_t k = 0; k < take;) {
+      const uint64_t slot = (first + k) % h->lo.rec_cap;
+      const uint64_t run = std::min<uint64_t>(take - k, h->lo.rec_cap - slot);
+      XY_CUDA(cudaMemcpyAsync(host_obs + (n_sweeps - take) + k, h->desc.rec + slot,
+                              run * sizeof(xy_obs), cudaMemcpyDeviceToHost, h->stream));
+      k += run;
+    }
+    h->reported = h->enqueued;
+  }
+  if (host_angles_out)
+    XY_CUDA(cudaMemcpyAsync(host_angles_out, h->desc.theta[cur1], ab, cudaMemcpyDeviceToHost,
+                            h->stream));
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+xy_status xy_profile(xy_lattice *h, int enable) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  h->prof = enable != 0;
+  h->ev_used = 0;
+  return XY_OK;
+}
+
+xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out) {
+  if (!h || !out) return fail(XY_EINVAL, "NULL argument");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  std::memset(out, 0, sizeof(*out));
+  // events come in groups of 6 per sweep
+  for (size_t base = 0; base + 6 <= h->ev_used; base += 6) {
+    for (int k = 0; k < XY_NUM_KERNELS; ++k) {
+      float ms = 0.0f;
+      XY_CUDA(cudaEventElapsedTime(&ms, h->events[base + k], h->events[base + k + 1]));
+      out->ms[k] += ms;
+      out->launches[k] += 1;
+    }
+  }
+  return XY_OK;
+}
+
+xy_status xy_get_angles(xy_lattice *h, void *host_dst) {
+  if (!h || !host_dst) return fail(XY_EINVAL, "NULL argument");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  DevState s;
+  XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
+  const size_t bytes = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
+  XY_CUDA(cudaMemcpy(host_dst, h->desc.theta[s.cur], bytes, cudaMemcpyDeviceToHost));
+  return XY_OK;
+}
+
+xy_status xy_set_angles(xy_lattice *h, const void *host_src) {
+  if (!h || !host_src) return fail(XY_EINVAL, "NULL argument");
+  const uint64_t n = static_cast<uint64_t>(h->lo.L) * h->lo.L;
+  const float two_pi = 6.2831854820251465f;
+  if (h->lo.esize == 4) {
+    const float *a = static_cast<const float *>(host_src);
+    for (uint64_t i = 0; i < n; ++i)
+      if (!(a[i] >= 0.0f && a[i] < two_pi))
+        return fail(XY_EINVAL, "angle %llu = %g outside [0, 2pi)",
+                    static_cast<unsigned long long>(i), a[i]);
+  } else {
+    const __half_raw *a = static_cast<const __half_raw *>(host_src);
+    for (uint64_t i = 0; i < n; ++i) {
+      const float v = __half2float(__half(a[i]));
+      if (!(v >= 0.0f && v < two_pi))
+        return fail(XY_EINVAL, "angle %llu = %g outside [0, 2pi)",
+                    static_cast<unsigned long long>(i), v);
+    }
+  }
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  DevState s;
+  XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
+  XY_CUDA(cudaMemcpy(h->desc.theta[s.cur], host_src, n * h->lo.esize, cudaMemcpyHostToDevice));
+  return XY_OK;
+}
+
+xy_status xy_get_bonds(xy_lattice *h, uint8_t *host_right, uint8_t *host_down) {
+  if (!h || !host_right || !host_down) return fail(XY_EINVAL, "NULL argument");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  const size_t words = static_cast<size_t>(h->lo.ntiles) * h->lo.TY;
+  std::vector<uint32_t> R(words), D(words);
+  XY_CUDA(cudaMemcpy(R.data(), h->desc.rplane, words * 4, cudaMemcpyDeviceToHost));
+  XY_CUDA(cudaMemcpy(D.data(), h->desc.dplane, words * 4, cudaMemcpyDeviceToHost));
+  const uint32_t L = h->lo.L, TY = h->lo.TY;
+  for (uint32_t tile = 0; tile < h->lo.ntiles; ++tile) {
+    const uint32_t x0 = (tile % h->lo.ntx) * 32, y0 = (tile / h->lo.ntx) * TY;
+    const uint32_t w = std::min(32u, L - x0), hh = std::min(TY, L - y0);
+    for (uint32_t r = 0; r < hh; ++r)
+      for (uint32_t c = 0; c < w; ++c) {
+        const size_t i = static_cast<size_t>(y0 + r) * L + x0 + c;
+        host_right[i] = (R[static_cast<size_t>(tile) * TY + r] >> c) & 1u;
+        host_down[i] = (D[static_cast<size_t>(tile) * TY + r] >> c) & 1u;
+      }
+  }
+  return XY_OK;
+}
+
+xy_status xy_get_labels(xy_lattice *h, uint32_t *host_dst) {
+  if (!h || !host_dst) return fail(XY_EINVAL, "NULL argument");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  XY_CUDA(cudaMemcpy(host_dst, h->desc.label, static_cast<size_t>(h->lo.L) * h->lo.L * 4,
+                     cudaMemcpyDeviceToHost));
+  return XY_OK;
+}
+
+xy_status xy_label_bonds(xy_lattice *h, const uint8_t *host_right, const uint8_t *host_down,
+                         uint32_t *host_labels) {
+  if (!h || !host_right || !host_down || !host_labels) return fail(XY_EINVAL, "NULL argument");
+  const uint32_t L = h->lo.L, TY = h->lo.TY;
+  const size_t words = static_cast<size_t>(h->lo.ntiles) * TY;
+  std::vector<uint32_t> R(words, 0u), D(words, 0u);
+  for (uint32_t tile = 0; tile < h->lo.ntiles; ++tile) {
+    const uint32_t x0 = (tile % h->lo.ntx) * 32, y0 = (tile / h->lo.ntx) * TY;
+    const uint32_t w = std::min(32u, L - x0), hh = std::min(TY, L - y0);
+    for (uint32_t r = 0; r < hh; ++r)
+      for (uint32_t c = 0; c < w; ++c) {
+        const size_t i = static_cast<size_t>(y0 + r) * L + x0 + c;
+        if (host_right[i] > 1 || host_down[i] > 1)
+          return fail(XY_EINVAL, "bond bytes must be 0 or 1");
+        R[static_cast<size_t>(tile) * TY + r] |= static_cast<uint32_t>(host_right[i]) << c;
+        D[static_cast<size_t>(tile) * TY + r] |= static_cast<uint32_t>(host_down[i]) << c;
+      }
+  }
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  XY_CUDA(cudaMemcpy(h->desc.rplane, R.data(), words * 4, cudaMemcpyHostToDevice));
+  XY_CUDA(cudaMemcpy(h->desc.dplane, D.data(), words * 4, cudaMemcpyHostToDevice));
+  XY_CUDA(launch_label_only(h));
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  xy_status s = check_device_error(h);
+  if (s != XY_OK) return s;
+  XY_CUDA(cudaMemcpy(host_labels, h->desc.label, static_cast<size_t>(L) * L * 4,
+                     cudaMemcpyDeviceToHost));
+  return XY_OK;
+}
+
+xy_status xy_get_band_stats(xy_lattice *h, uint64_t *n_fp64, uint64_t *n_fp32_wrong) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  DevState s;
+  XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
+  if (n_fp64) *n_fp64 = s.n_fp64;
+  if (n_fp32_wrong) *n_fp32_wrong = s.n_fp32_wrong;
+  return XY_OK;
+}
+
+// Checkpoint blob: header, device state, angles.
+struct CkptHeader {
+  char magic[8];
+  uint32_t L, dtype, thr, tile_y;
+  uint64_t seed;
+  uint64_t enqueued;
+  uint64_t state_bytes, angle_bytes;
+};
+
+xy_status xy_save(xy_lattice *h, void *host_blob, size_t *bytes) {
+  if (!h || !bytes) return fail(XY_EINVAL, "NULL argument");
+  const size_t ab = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
+  const size_t need = sizeof(CkptHeader) + sizeof(DevState) + ab;
+  if (!host_blob) {
+    *bytes = need;
+    return XY_OK;
+  }
+  if (*bytes < need) return fail(XY_ENOMEM, "blob of %zu bytes, %zu needed", *bytes, need);
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  char *p = static_cast<char *>(host_blob);
+  CkptHeader hd;
+  std::memcpy(hd.magic, "XYSWCK01", 8);
+  hd.L = h->lo.L;
+  hd.dtype = static_cast<uint32_t>(h->cfg.angle_dtype);
+  hd.thr = static_cast<uint32_t>(h->cfg.threshold_mode);
+  hd.tile_y = h->lo.TY;
+  hd.seed = h->cfg.seed;
+  hd.enqueued = h->enqueued;
+  hd.state_bytes = sizeof(DevState);
+  hd.angle_bytes = ab;
+  std::memcpy(p, &hd, sizeof(hd));
+  DevState s;
+  XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
+  std::memcpy(p + sizeof(hd), &s, sizeof(s));
+  XY_CUDA(cudaMemcpy(p + sizeof(hd) + sizeof(s), h->desc.theta[s.cur], ab,
+                     cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return XY_OK;
+}
+
+xy_status xy_load(xy_lattice *h, const void *host_blob, size_t bytes) {
+  if (!h || !host_blob) return fail(XY_EINVAL, "NULL argument");
+  const size_t ab = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
+  if (bytes < sizeof(CkptHeader) + sizeof(DevState) + ab)
+    return fail(XY_EINVAL, "blob too small");
+  const char *p = static_cast<const char *>(host_blob);
+  CkptHeader hd;
+  std::memcpy(&hd, p, sizeof(hd));
+  if (std::memcmp(hd.magic, "XYSWCK01", 8) != 0) return fail(XY_EINVAL, "not a checkpoint");
+  if (hd.L != h->lo.L || hd.dtype != static_cast<uint32_t>(h->cfg.angle_dtype) ||
+      hd.seed != h->cfg.seed || hd.state_bytes != sizeof(DevState) || hd.angle_bytes != ab)
+    return fail(XY_EINVAL, "checkpoint does not match this lattice (L, dtype or seed)");
+  DevState s;
+  std::memcpy(&s, p + sizeof(hd), sizeof(s));
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  XY_CUDA(cudaMemcpy(h->desc.theta[s.cur], p + sizeof(hd) + sizeof(s), ab,
+                     cudaMemcpyHostToDevice));
+  XY_CUDA(cudaMemcpy(h->d_state, &s, sizeof(s), cudaMemcpyHostToDevice));
+  XY_CUDA(cudaMemset(h->desc.acc, 0, sizeof(long long) * kSlots * kAccStride));
+  h->enqueued = hd.enqueued;
+  h->reported = hd.enqueued;
+  return XY_OK;
+}
+
+}  // extern "C"
