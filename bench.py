@@ -1,0 +1,383 @@
+"""Benchmark of the Swendsen-Wang XY sweep on B300: one JSON line.
+
+A step is one full SW sweep (axis, bonds, labels, flip, observables, record)
+of an L = 4096 periodic lattice (16.8M spins, FP32 angles, beta = 1.12,
+Philox random start) -- the single-lattice workload the spin-updates/ns metric
+is quoted on.  The working set of a sweep (two angle buffers, labels, bit
+planes: 204 MB) is larger than the 126 MB L2, so sweeps run back to back
+without an explicit flush.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own independent lattice (replicas
+only: the method has no data-path exchange); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "spin updates/ns per SW sweep (L=4096, 65536) & %HBM roofline; batched sweeps/s, p50/p99"
+UNIT = "spin updates/ns"
+
+# Algorithmic bytes per site of each kernel (FP32 angles): what the step must
+# move at minimum for that kernel's share of the work.
+KERNEL_BYTES_PER_SITE = {
+    "bond_label": 4.0 + 4.0 + 0.25 + 0.125,   # angles in, tile labels out, bond planes, coin bits
+    "flip_measure": 4.0 + 4.0 + 4.0 + 4.0,    # labels in/out, angles in/out
+}
+# Whole-sweep byte models (per site): the method's minimum with canonical
+# labels materialised, and the pipeline this library runs.
+M_CANON = 16.5
+M_BUILT = 4.0 + 4.0 + 0.375 + 16.0
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.samples = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.samples.append(f)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1210_6116_b300 as xy
+    from paper_1210_6116_b300 import build as xybuild
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    if rank == 0:
+        xybuild.build()
+    if pg:
+        pg.barrier()
+    L, beta = args.L, args.beta
+    N = L * L
+    lat = xy.Lattice(L, beta, seed=1000 + rank, tile_y=args.tile_y, exact=bool(args.exact))
+    stream = lat.stream
+    lat.sweep(args.warmup)
+    lat.measure(max_records=0)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    lat.profile(True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        done = 0
+        while done < args.steps:
+            n = min(1024, args.steps - done)
+            lat.sweep(n)
+            done += n
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kt = lat.profile_read()
+    lat.profile(False)
+    recs = lat.measure()
+    t_sec = ms / 1e3
+    if pg:
+        tt = torch.tensor([t_sec], device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_sec = float(tt.item())
+    value = ws * N * args.steps / (t_sec * 1e9)
+    ms_per_step = t_sec * 1e3 / args.steps
+    launches = 5 * args.steps + math.ceil(args.steps / 1024)
+
+    out = None
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        # dominant kernel
+        dom = max(KERNEL_BYTES_PER_SITE, key=lambda k: kt[k][0])
+        dms = kt[dom][0] / kt[dom][1]
+        dbytes = KERNEL_BYTES_PER_SITE[dom] * N
+        achieved = dbytes / (dms * 1e-3) / 1e9
+        kernels = {k: {"ms_per_launch": round(v[0] / v[1], 5), "share": round(v[0] / sum(x[0] for x in kt.values()), 4)}
+                   for k, v in kt.items()}
+        traffic = None
+        tfile = ROOT / "profiles" / "traffic.json"
+        if tfile.exists():
+            import hashlib
+            tj = json.loads(tfile.read_text())
+            src = ROOT / "paper_1210_6116_b300" / "csrc" / "sweep_kernels.cuh"
+            same = hashlib.sha256(src.read_bytes()).hexdigest()[:16] == tj.get("kernels_source_sha256_16")
+            if same and tj.get("kernel") == dom and tj.get("L") == L:
+                traffic = tj.get("bytes_per_launch")
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"SW sweep, 2D XY, L={L} periodic ({N} spins), beta={beta}, "
+                                   "FP32 angles, Philox random start",
+                       "L": L, "beta": beta, "tile": f"32x{lat.cfg.tile_y or 'auto'}",
+                       "thresholds": "fp64-exact" if args.exact else "fp32",
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "working set 204 MB > 126 MB L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "bytes_per_site": KERNEL_BYTES_PER_SITE[dom]},
+            "sweep_roofline": {"model_canon_B_per_site": M_CANON, "model_built_B_per_site": M_BUILT,
+                               "frac_canon": round(value * M_CANON / peak, 4),
+                               "frac_built": round(value * M_BUILT / peak, 4)},
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "last_energy_per_site": float(recs[-1]["energy_per_site"]) if len(recs) else None,
+        }
+    # end to end through the C ABI with pinned host buffers
+    e2e = run_e2e(lat, args, N)
+    if rank == 0:
+        out["e2e"] = e2e
+        if args.exact_report:
+            out["exact_mode"] = exact_report(xy, L, beta, args)
+        if args.big and ws == 1:
+            out["l65536"] = run_big(xy, args)
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(out), flush=True)
+    lat.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def run_e2e(lat, args, N):
+    import numpy as np
+    import torch
+
+    import paper_1210_6116_b300 as xy
+
+    n_steps = max(3, min(args.e2e_steps, args.steps))
+    host_in = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    host_in.numpy()[:] = lat.get_angles()
+    obs = np.zeros(1, xy.OBS_DTYPE)
+    obs_pinned = torch.empty(obs.nbytes, dtype=torch.uint8, pin_memory=True)
+    a_in = host_in.numpy()
+    o_out = obs_pinned.numpy().view(xy.OBS_DTYPE)
+    lat.run_host(a_in, 1, o_out)  # warm
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        lat.run_host(a_in, 1, o_out)
+    dt = (time.perf_counter() - t0) / n_steps
+    return {"value": round(N / (dt * 1e9), 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+            "d2h_bytes_per_step": int(obs.nbytes), "steps": n_steps,
+            "how": "xy_run_host per step: pinned host angles in, one sweep, the sweep's record out"}
+
+
+def exact_report(xy, L, beta, args):
+    import torch
+
+    lat = xy.Lattice(L, beta, seed=4242, tile_y=args.tile_y, exact=True)
+    lat.sweep(5)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = max(20, min(200, args.steps))
+    e0.record(lat.stream)
+    lat.sweep(n)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    n64, wrong = lat.band_stats()
+    bonds = 2 * L * L * (n + 5)
+    lat.close()
+    return {"value": round(L * L / (ms * 1e6), 3), "unit": UNIT, "ms_per_step": round(ms, 5),
+            "fp64_band_fraction": n64 / bonds, "fp32_bond_mismatch_rate": wrong / bonds}
+
+
+def run_big(xy, args):
+    import torch
+
+    L = 65536
+    free, total = torch.cuda.mem_get_info()
+    cfg_bytes = xy.xy_workspace_size(xy.xy_config(L=L, tile_y=args.tile_y, seed=2, beta=1.1199,
+                                                  angle_dtype=0, threshold_mode=args.exact,
+                                                  start=1, record_cap=0))
+    if cfg_bytes > 0.9 * free:
+        return {"skipped": f"needs {cfg_bytes/1e9:.1f} GB, {free/1e9:.1f} GB free"}
+    lat = xy.Lattice(L, 1.1199, seed=2, start="ordered", tile_y=args.tile_y, exact=bool(args.exact))
+    lat.sweep(2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = args.big_steps
+    lat.profile(True)
+    e0.record(lat.stream)
+    lat.sweep(n)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    kt = lat.profile_read()
+    lat.profile(False)
+    ms = e0.elapsed_time(e1) / n
+    recs = lat.measure()
+    peak, _ = _peaks()
+    v = L * L / (ms * 1e6)
+    out = {"value": round(v, 3), "unit": UNIT, "ms_per_step": round(ms, 4), "steps": n,
+           "beta": 1.1199, "start": "ordered",
+           "frac_canon": round(v * M_CANON / peak, 4), "frac_built": round(v * M_BUILT / peak, 4),
+           "bytes_per_sweep_model_canon": M_CANON * L * L,
+           "kernels_ms": {k: round(val[0] / val[1], 4) for k, val in kt.items()},
+           "last_energy_per_site": float(recs[-1]["energy_per_site"])}
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    L = args.L
+    th = oracle.init_angles(L, 1000, 0)
+    n = args.cpu_sweeps
+    t0 = time.perf_counter()
+    oracle.sw_run(th, L, L, args.beta, 1000, 0, n)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * L * L / (dt * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} sweeps of the L={L} lattice (beta={args.beta}), {dt:.1f} s",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    # bounded sample: one sweep of an L_s x L_s lattice per step, L_s the
+    # largest power of two with an estimated run under ~90 s (230 ns/site)
+    total = args.steps + args.warmup
+    L_s = 64
+    while L_s * 2 <= args.L and total * (2 * L_s) ** 2 * 230e-9 < 90.0:
+        L_s *= 2
+    th = oracle.init_angles(L_s, 1000, 0)
+    oracle.sw_run(th, L_s, L_s, args.beta, 1000, 0, args.warmup, record=False)
+    t0 = time.perf_counter()
+    oracle.sw_run(th, L_s, L_s, args.beta, 1000, args.warmup, args.steps, record=False)
+    dt = time.perf_counter() - t0
+    v = args.steps * L_s * L_s / (dt * 1e9)
+    sample = f"{args.steps} sweeps of an L={L_s} lattice (beta={args.beta}) per run, one sweep per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"SW sweep, 2D XY, L={args.L} periodic, beta={args.beta} "
+                               f"(timed on an L={L_s} sample)", "L": args.L, "beta": args.beta},
+        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=4096)
+    ap.add_argument("--beta", type=float, default=1.12)
+    ap.add_argument("--tile-y", dest="tile_y", type=int, default=64)
+    ap.add_argument("--exact", type=int, default=0)
+    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=50)
+    ap.add_argument("--cpu-sweeps", dest="cpu_sweeps", type=int, default=3)
+    ap.add_argument("--big-steps", dest="big_steps", type=int, default=10)
+    ap.add_argument("--no-big", dest="big", action="store_false")
+    ap.add_argument("--no-cpu", dest="no_cpu", action="store_true")
+    ap.add_argument("--no-exact-report", dest="exact_report", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -202,12 +202,16 @@ __device__ __noinline__ bool bond_fp64(float th_i, float th_j, uint32_t word,
 
 // ---------------------------------------------------------------------------
 // shared-memory union-find on tile-local indices (r*32 + c).  Every link
-// points to a strictly smaller index, so finds terminate.
+// points to a strictly smaller index, so finds terminate.  Finds halve the
+// path: a node is re-pointed at its grandparent, which is always an ancestor,
+// so concurrent halving and CAS linking of roots never lose a union.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sfind(volatile uint32_t *par, uint32_t a) {
   uint32_t p = par[a];
   while (p != a) {
-    a = p;
+    const uint32_t gp = par[p];
+    if (gp != p) par[a] = gp;
+    a = gp;
     p = par[a];
   }
   return a;
@@ -293,24 +297,48 @@ __device__ __forceinline__ void tile_label(const Tile &g, uint32_t L,
                                            uint32_t *label) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rmask = (g.w >= 32u) ? 0x7FFFFFFFu : ((1u << (g.w - 1u)) - 1u);
+  const bool col_ok = lane < static_cast<int>(g.w);
+  // every site points at the start of its row run; run starts are roots
   for (uint32_t r = warp; r < g.h; r += kWarps) {
-    if (lane < static_cast<int>(g.w)) {
+    if (col_ok) {
       const uint32_t starts = ~((sR[r] & rmask) << 1);
       const uint32_t s = 31u - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
       par[r * 32u + lane] = r * 32u + s;
     }
   }
   __syncthreads();
-  for (uint32_t r = warp; r + 1u < g.h; r += kWarps) {
-    const uint32_t D = sD[r];
-    const uint32_t V = D & ~((D & sR[r] & sR[r + 1] & rmask) << 1);
-    if (lane < static_cast<int>(g.w) && ((V >> lane) & 1u))
-      sunion(par, r * 32u + lane, (r + 1u) * 32u + lane);
+  // Vertical unions, merged hierarchically: at span s, row blocks
+  // [2ks, 2ks + s) and [2ks + s, 2ks + 2s) join across their boundary row
+  // pair only.  Boundaries of one level touch disjoint node sets, and a
+  // node is at most one link per level from its block root, so trees stay
+  // log2(TY) deep.  One union per pair of vertically touching runs (the
+  // first column where they touch).
+  for (uint32_t span = 1; span < g.h; span <<= 1) {
+    const uint32_t nb = (g.h - span + 2u * span - 1u) / (2u * span);
+    for (uint32_t b = warp; b < nb; b += kWarps) {
+      const uint32_t r = b * 2u * span + span - 1u;
+      if (r + 1u < g.h) {
+        const uint32_t D = sD[r];
+        const uint32_t V = D & ~((D & sR[r] & sR[r + 1] & rmask) << 1);
+        if (col_ok && ((V >> lane) & 1u))
+          sunion(par, r * 32u + lane, (r + 1u) * 32u + lane);
+      }
+    }
+    __syncthreads();
+  }
+  // run starts point straight at their root; every other site is then two
+  // hops from it (all ancestors of a site are run starts)
+  for (uint32_t r = warp; r < g.h; r += kWarps) {
+    const uint32_t starts = ~((sR[r] & rmask) << 1);
+    if (col_ok && ((starts >> lane) & 1u)) {
+      const uint32_t node = r * 32u + lane;
+      par[node] = sfind(par, node);
+    }
   }
   __syncthreads();
   for (uint32_t r = warp; r < g.h; r += kWarps) {
-    if (lane < static_cast<int>(g.w)) {
-      const uint32_t root = sfind(par, r * 32u + lane);
+    if (col_ok) {
+      const uint32_t root = par[par[r * 32u + lane]];
       label[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] =
           (g.y0 + (root >> 5)) * L + g.x0 + (root & 31u);
     }
@@ -350,13 +378,29 @@ __global__ void __launch_bounds__(kThreads)
       const uint32_t t = st->t;
       const AT *th = static_cast<const AT *>(d.theta[st->cur]);
       const float cphi = st->cphi32, sphi = st->sphi32;
-      // projections of the tile plus its right column and bottom row
-      for (uint32_t r = warp; r <= g.h; r += kWarps) {
-        const uint64_t row = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L;
-        if (lane < static_cast<int>(g.w))
-          sa[r][lane] = project32(load_angle(th, row + g.x0 + lane), cphi, sphi);
-        if (lane == 0) sa[r][g.w] = project32(load_angle(th, row + g.xh), cphi, sphi);
+      // projections of the tile plus its right column and bottom row; all
+      // loads of a thread are issued before the first use
+      // (thread t < h also loads row t of the column right of the tile)
+      constexpr int KR = TY / kWarps + 1;
+      float tv[KR];
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const uint32_t r = warp + k * kWarps;
+        tv[k] = 0.0f;
+        if (r <= g.h && lane < static_cast<int>(g.w)) {
+          const uint64_t row = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L;
+          tv[k] = load_angle(th, row + g.x0 + lane);
+        }
       }
+      const bool hc = threadIdx.x < g.h;
+      float thc = 0.0f;
+      if (hc) thc = load_angle(th, static_cast<uint64_t>(g.y0 + threadIdx.x) * L + g.xh);
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const uint32_t r = warp + k * kWarps;
+        if (r <= g.h && lane < static_cast<int>(g.w)) sa[r][lane] = project32(tv[k], cphi, sphi);
+      }
+      if (hc) sa[threadIdx.x][g.w] = project32(thc, cphi, sphi);
       __syncthreads();
       const float b2 = st->beta2_32, eps = st->eps;
       for (uint32_t r = warp; r < g.h; r += kWarps) {
@@ -434,16 +478,27 @@ __global__ void __launch_bounds__(kThreads)
 // K2: merge across tile edges.  Work item = (tile, j): j < TY is the right
 // edge of tile row j, j >= TY the bottom edge of column j - TY.
 // ---------------------------------------------------------------------------
+// An edge bond is skipped when the previous edge of the same side is active
+// and both pairs of endpoints are joined by a direct bond along the edge: the
+// previous edge then unites the same two clusters.
 template <int TY>
 __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
                                           uint32_t j, uint32_t *a,
                                           uint32_t *b) {
   const uint32_t L = d.L;
   const Tile g = tile_geom<TY>(L, d.ntx, tile);
+  const uint64_t base = static_cast<uint64_t>(tile) * TY;
   if (j < static_cast<uint32_t>(TY)) {
     if (j >= g.h) return false;
-    const uint32_t R = __ldg(d.rplane + static_cast<uint64_t>(tile) * TY + j);
-    if (!((R >> (g.w - 1u)) & 1u)) return false;
+    const uint32_t bit = g.w - 1u;
+    if (!((__ldg(d.rplane + base + j) >> bit) & 1u)) return false;
+    if (j > 0 && ((__ldg(d.rplane + base + j - 1) >> bit) & 1u) &&
+        ((__ldg(d.dplane + base + j - 1) >> bit) & 1u)) {
+      // the neighbouring tile to the right holds column xh at bit 0
+      const uint32_t tx = tile % d.ntx;
+      const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
+      if (__ldg(d.dplane + static_cast<uint64_t>(tn) * TY + j - 1) & 1u) return false;
+    }
     const uint32_t y = g.y0 + j;
     *a = y * L + g.x0 + g.w - 1u;
     *b = y * L + g.xh;
@@ -451,8 +506,15 @@ __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
   }
   const uint32_t c = j - TY;
   if (c >= g.w) return false;
-  const uint32_t D = __ldg(d.dplane + static_cast<uint64_t>(tile) * TY + g.h - 1u);
+  const uint32_t D = __ldg(d.dplane + base + g.h - 1u);
   if (!((D >> c) & 1u)) return false;
+  if (c > 0 && ((D >> (c - 1u)) & 1u) &&
+      ((__ldg(d.rplane + base + g.h - 1u) >> (c - 1u)) & 1u)) {
+    // the tile below holds row yh as its row 0, same columns
+    const uint32_t ty = tile / d.ntx;
+    const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tile % d.ntx;
+    if ((__ldg(d.rplane + static_cast<uint64_t>(tb) * TY) >> (c - 1u)) & 1u) return false;
+  }
   *a = (g.y0 + g.h - 1u) * L + g.x0 + c;
   *b = g.yh * L + g.x0 + c;
   return true;
@@ -472,19 +534,34 @@ __global__ void __launch_bounds__(kThreads)
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
   uint32_t a, b;
-  if (edge_bond<TY>(d, tile, j, &a, &b)) gunion(d.label, a, b, d.st);
+  // start from the tile roots: labels of non-root sites are never written
+  // here, so after the merge every site still points at its tile root
+  if (edge_bond<TY>(d, tile, j, &a, &b))
+    gunion(d.label, __ldcg(d.label + a), __ldcg(d.label + b), d.st);
 }
 
-// K3: after all unions, point every node on the path from an edge site to
-// its root directly at the root (roots no longer change).
+// K3: after all unions, every merged tile root re-points at its grandparent
+// until its parent is a root.  All merged tile roots jump concurrently, so a
+// chain of length d collapses in O(log d) steps per node instead of a walk of
+// length d.  Only ancestors are ever written and roots no longer change.
+__device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st) {
+  for (uint32_t it = 0; it < kFindCap; ++it) {
+    const uint32_t p = __ldcg(lab + x);
+    if (p == x) return;
+    const uint32_t gp = __ldcg(lab + p);
+    if (gp == p) return;
+    __stcg(lab + x, gp);
+  }
+  atomicOr(&st->err, kErrFindCap);
+}
+
 __device__ __forceinline__ void compress(uint32_t *lab, uint32_t a,
                                          DevState *st) {
-  const uint32_t root = gfind_ro(lab, a, st);
-  for (uint32_t it = 0; it < kFindCap && a != root; ++it) {
-    const uint32_t p = __ldcg(lab + a);
-    __stcg(lab + a, root);
-    a = p;
-  }
+  // a is an edge site: jump its tile root (its label, unless a is itself a
+  // tile root whose entry the merge already moved) and a itself
+  const uint32_t t = __ldcg(lab + a);
+  jump(lab, t, st);
+  jump(lab, a, st);
 }
 
 template <int TY>
@@ -530,6 +607,9 @@ __global__ void __launch_bounds__(kThreads)
   float2(*cs)[33] = reinterpret_cast<float2(*)[33]>(smem);
   __shared__ long long red[kWarps][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // a thread handles rows r = warp + 8k (k < KR, r <= h): column `lane` of
+  // the tile (and of the row below it), and lane 0 also column xh of rows < h
+  constexpr int KR = TY / kWarps + 1;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
     const uint32_t rep = find_rep(prefix, nrep, work);
@@ -543,46 +623,95 @@ __global__ void __launch_bounds__(kThreads)
     const AT *thin = static_cast<const AT *>(d.theta[cur]);
     AT *thout = static_cast<AT *>(d.theta[cur ^ 1u]);
     uint32_t *lab = d.label;
+    const bool col_ok = lane < static_cast<int>(g.w);
 
-    // pass 1: flipped angles of the tile, its right column and bottom row
-    for (uint32_t r = warp; r <= g.h; r += kWarps) {
-      const uint32_t gy = r < g.h ? g.y0 + r : g.yh;
-      const uint64_t row = static_cast<uint64_t>(gy) * L;
-      for (int part = 0; part < 2; ++part) {
-        uint32_t c;
-        if (part == 0) {
-          if (lane >= static_cast<int>(g.w)) continue;
-          c = lane;
-        } else {
-          if (lane != 0 || r == g.h) continue;
-          c = g.w;
-        }
-        const uint32_t gx = c < g.w ? g.x0 + c : g.xh;
-        const uint64_t i = row + gx;
-        const uint32_t root = gfind_ro(lab, __ldcg(lab + i), st);
-        const bool own = (r < g.h) && (c < g.w);
-        if (own) __stcg(lab + i, root);
-        if (LABELS_ONLY) continue;
-        const bool flip = (__ldg(d.coin + (root >> 5)) >> (root & 31u)) & 1u;
-        const float th = load_angle(thin, i);
-        float nv = th;
-        if (flip) {
-          const AT sv = store_value<AT>(wrap_angle(__fadd_rn(c32, -th)));
+    // round 1: labels and angles.  Positions of this thread: rows
+    // r = warp + 8k (k < KR, r <= h) at column `lane`, and -- for threads
+    // t < h -- row t of the column right of the tile (xh).
+    uint32_t l0[KR];
+    float t0[KR];
+    bool v0[KR];
+    const bool vh = threadIdx.x < g.h;
+    const uint64_t ih = static_cast<uint64_t>(g.y0 + threadIdx.x) * L + g.xh;
+    uint32_t lh = 0u;
+    float th_h = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const uint32_t r = warp + k * kWarps;
+      v0[k] = (r <= g.h) && col_ok;
+      const uint64_t row = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L;
+      l0[k] = 0u;
+      t0[k] = 0.0f;
+      if (v0[k]) {
+        l0[k] = __ldcg(lab + row + g.x0 + lane);
+        if (!LABELS_ONLY) t0[k] = load_angle(thin, row + g.x0 + lane);
+      }
+    }
+    if (vh) {
+      lh = __ldcg(lab + ih);
+      if (!LABELS_ONLY) th_h = load_angle(thin, ih);
+    }
+    // round 2: one more hop (the tile root's entry)
+    uint32_t p0[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) p0[k] = v0[k] ? __ldcg(lab + l0[k]) : 0u;
+    const uint32_t ph = vh ? __ldcg(lab + lh) : 0u;
+    // round 3: where the tile root was merged, confirm the next node is the
+    // root (the usual case after k_compress) or finish the find
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (v0[k] && p0[k] != l0[k]) {
+        const uint32_t q = __ldcg(lab + p0[k]);
+        l0[k] = (q == p0[k]) ? q : gfind_ro(lab, q, st);
+      }
+    }
+    if (vh && ph != lh) {
+      const uint32_t q = __ldcg(lab + ph);
+      lh = (q == ph) ? q : gfind_ro(lab, q, st);
+    }
+    // l0 / lh now hold the roots; own sites get their canonical label
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const uint32_t r = warp + k * kWarps;
+      if (v0[k] && r < g.h)
+        __stcg(lab + static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane, l0[k]);
+    }
+    if (LABELS_ONLY) continue;
+    // round 4: coins of the roots
+    uint32_t f0[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+      f0[k] = v0[k] ? (__ldg(d.coin + (l0[k] >> 5)) >> (l0[k] & 31u)) & 1u : 0u;
+    const uint32_t fh = vh ? (__ldg(d.coin + (lh >> 5)) >> (lh & 31u)) & 1u : 0u;
+    // flip, store, and cos/sin of the new angles into shared memory
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const uint32_t r = warp + k * kWarps;
+      if (v0[k]) {
+        float nv = t0[k];
+        if (f0[k]) {
+          const AT sv = store_value<AT>(wrap_angle(__fadd_rn(c32, -t0[k])));
           nv = stored_float<AT>(sv);
-          if (own) thout[i] = sv;
-        } else if (own) {
-          thout[i] = store_value<AT>(th);
+          if (r < g.h) thout[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] = sv;
+        } else if (r < g.h) {
+          thout[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] = store_value<AT>(t0[k]);
         }
         float s, co;
         sincosf(nv, &s, &co);
-        cs[r][c] = make_float2(co, s);
+        cs[r][lane] = make_float2(co, s);
       }
     }
-    if (LABELS_ONLY) continue;
+    if (vh) {
+      float nv = th_h;
+      if (fh) nv = stored_float<AT>(store_value<AT>(wrap_angle(__fadd_rn(c32, -th_h))));
+      float s, co;
+      sincosf(nv, &s, &co);
+      cs[threadIdx.x][g.w] = make_float2(co, s);
+    }
     __syncthreads();
-    // pass 2: terms of the tile's own sites
+    // terms of the tile's own sites
     int acc[6] = {0, 0, 0, 0, 0, 0};
-    if (lane < static_cast<int>(g.w)) {
+    if (col_ok) {
       for (uint32_t r = warp; r < g.h; r += kWarps) {
         const float2 a = cs[r][lane], rr = cs[r][lane + 1], dd = cs[r + 1][lane];
         acc[0] += fix22(a.x);
@@ -607,12 +736,12 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
     if (threadIdx.x < 6) {
-      long long s = 0;
+      long long sum = 0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+      for (int w = 0; w < kWarps; ++w) sum += red[w][threadIdx.x];
       atomicAdd(reinterpret_cast<unsigned long long *>(
                     d.acc + (tile % kSlots) * kAccStride + threadIdx.x),
-                static_cast<unsigned long long>(s));
+                static_cast<unsigned long long>(sum));
     }
     __syncthreads();
   }
