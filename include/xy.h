@@ -205,6 +205,32 @@ xy_status xy_profile(xy_lattice *h, int enable);
 /* Synchronise and return the totals since profiling was enabled. */
 xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out);
 
+/* ---- labeling without any device allocation ------------------------------ */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory and therefore cannot provide the workspace
+ * of a lattice handle -- e.g. a plugin that its host application hands only
+ * input and output buffers, or a real-time loop that forbids allocation.
+ *
+ * Labels the bonds d_right / d_down (device arrays of L*L bytes, nonzero =
+ * active, same meaning as xy_get_bonds) of an L x L periodic lattice into
+ * d_labels (device array of L*L uint32: minimum site index of each cluster),
+ * with the same kernels as xy_label_bonds.  Its scratch is a fixed array
+ * built into the library (about 0.26 MB on every GPU that loads it, kept
+ * until the process exits); it calls no cudaMalloc/cudaFree.
+ *   - L is limited to 2..XY_STATIC_MAX_L; larger L returns XY_EINVAL.
+ *   - The first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) for that device; make that first call before
+ *     any stream capture.
+ *   - All calls share the scratch: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and give wrong labels.
+ *   - Work is enqueued on cuda_stream; sync = 1 waits for it and reports a
+ *     device-side loop bound as XY_ETIMEOUT, sync = 0 returns after
+ *     enqueueing (errors then go unreported). */
+#define XY_STATIC_MAX_L 1024u
+xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right,
+                                const uint8_t *d_down, uint32_t *d_labels,
+                                void *cuda_stream, int sync);
+
 /* ---- checkpoint --------------------------------------------------------- */
 /* Serialise the full chain state (angles, seed, sweep counter, beta, PCC
  * accumulators, dtype) into host memory.  Call with blob = NULL to get the

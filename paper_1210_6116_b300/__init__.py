@@ -33,7 +33,7 @@ EXPORTS = (
     "xy_last_error", "xy_workspace_size", "xy_init", "xy_sweep", "xy_pcc_step",
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
     "xy_get_bonds", "xy_get_labels", "xy_label_bonds", "xy_get_band_stats", "xy_save",
-    "xy_load", "xy_run_host", "xy_profile", "xy_profile_read",
+    "xy_load", "xy_run_host", "xy_profile", "xy_profile_read", "xy_label_bonds_static",
 )
 KERNEL_NAMES = ("bond_label", "merge", "compress", "flip_measure", "finalize")
 
@@ -104,6 +104,7 @@ def load_library() -> ctypes.CDLL:
         "xy_run_host": (I, [P, P, U32, P, P]),
         "xy_profile": (I, [P, I]),
         "xy_profile_read": (I, [P, P]),
+        "xy_label_bonds_static": (I, [U32, P, P, P, P, I]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -168,6 +169,19 @@ def xy_destroy(h):
 
 def xy_last_error() -> str:
     return load_library().xy_last_error().decode()
+
+
+XY_STATIC_MAX_L = 1024
+
+
+def xy_label_bonds_static(L: int, d_right: int, d_down: int, d_labels: int, stream: int,
+                          sync: int = 1):
+    """Label device bond bytes into device labels without any workspace
+    (see include/xy.h): pointers are device addresses."""
+    _check(load_library().xy_label_bonds_static(L, ctypes.c_void_p(d_right),
+                                                ctypes.c_void_p(d_down),
+                                                ctypes.c_void_p(d_labels),
+                                                ctypes.c_void_p(stream), sync))
 
 
 # ---------------------------------------------------------------------------

@@ -32,9 +32,9 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         return LIB
     tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
     cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC",
+           "-Xcompiler", "-fPIC", "-diag-suppress", "128",
            "-I", str(ROOT / "include"),
-           str(SRC / "xy_api.cu"), "-o", str(tmp)]
+           str(SRC / "xy_api.cu"), str(SRC / "xy_static.cu"), "-o", str(tmp)]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

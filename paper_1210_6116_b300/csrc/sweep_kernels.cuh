@@ -188,7 +188,7 @@ __device__ __forceinline__ Tile tile_geom(uint32_t L, uint32_t ntx,
 // ---------------------------------------------------------------------------
 // FP64 rule, operation for operation: x = a_i a_j; active iff x > 0 and
 // (w + 1/2) 2^-32 < 1 - exp(-2 beta x).
-__device__ __noinline__ bool bond_fp64(float th_i, float th_j, uint32_t word,
+static __device__ __noinline__ bool bond_fp64(float th_i, float th_j, uint32_t word,
                                        double beta, double cphi, double sphi) {
   const double ai = project64(th_i, cphi, sphi);
   const double aj = project64(th_j, cphi, sphi);
@@ -775,7 +775,7 @@ __device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta,
 }
 
 // K5: one warp per lattice
-__global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
+static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
   const uint32_t rep = blockIdx.x;
   if (rep >= nrep) return;
   const LatDesc &d = descs[rep];
@@ -855,7 +855,7 @@ __global__ void k_init_angles(LatDesc d, int ordered) {
   }
 }
 
-__global__ void k_init_state(LatDesc d, double beta) {
+static __global__ void k_init_state(LatDesc d, double beta) {
   DevState *st = d.st;
   st->cur = 0;
   st->pcc_on = 0;
@@ -873,7 +873,7 @@ __global__ void k_init_state(LatDesc d, double beta) {
   set_sweep_params(st, 0u, beta, d.key0, d.key1);
 }
 
-__global__ void k_set_pcc(DevState *st, uint32_t on, double target,
+static __global__ void k_set_pcc(DevState *st, uint32_t on, double target,
                           double dbeta0, uint32_t halve, uint32_t block) {
   st->pcc_on = on;
   if (on) {

@@ -102,6 +102,11 @@ xy_status make_layout(const xy_config *c, Layout *lo) {
 
 }  // namespace
 
+// Sets the calling thread's xy_last_error() message (used by xy_static.cu).
+void xy_set_last_error_message(const char *msg) {
+  snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
 struct xy_lattice {
   xy_config cfg;
   Layout lo;

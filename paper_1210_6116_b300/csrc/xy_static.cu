@@ -1,0 +1,169 @@
+// xy_static.cu -- cluster labeling of caller-supplied bonds that allocates
+// nothing: its scratch lives in a fixed array compiled into the library.
+//
+// Who this is for: callers that cannot allocate device memory, and so cannot
+// hand xy_init the workspace a lattice handle needs -- for example a plugin
+// that its host application gives only the input and output buffers, or a
+// real-time loop whose rules forbid device allocation once it runs.  They
+// pass device pointers to the bonds and to the output labels; everything
+// else comes from `g_label_scratch` below.
+//
+// The scratch array is a file-scope __device__ array, so every GPU that
+// loads this library holds it (about 0.26 MB) until the process exits.  All
+// calls share it and it keeps the contents of the last call: every call
+// rewrites the parts it reads (descriptor, state word, bit planes) before
+// using them, and calls whose work overlaps on the GPU (two streams, or two
+// host threads at once) race on it and give wrong labels.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/xy.h"
+#include "sweep_kernels.cuh"
+
+using namespace xyk;
+
+// defined in xy_api.cu: the thread's xy_last_error() message
+void xy_set_last_error_message(const char *msg);
+
+namespace {
+
+constexpr uint32_t kStaticTile = 32;  // labeling tile 32 x 32
+constexpr uint32_t kStaticMaxTiles =
+    (XY_STATIC_MAX_L / 32) * (XY_STATIC_MAX_L / kStaticTile);
+constexpr size_t kPlaneWords = static_cast<size_t>(kStaticMaxTiles) * kStaticTile;
+
+// layout of the scratch array (byte offsets, each 256-aligned)
+constexpr size_t kOffDesc = 0;
+constexpr size_t kOffPrefix = 256;
+constexpr size_t kOffState = 512;
+constexpr size_t kOffRplane = 1024;
+constexpr size_t kOffDplane = kOffRplane + kPlaneWords * sizeof(uint32_t);
+constexpr size_t kScratchBytes = kOffDplane + kPlaneWords * sizeof(uint32_t);
+static_assert(sizeof(LatDesc) <= 256 && sizeof(DevState) <= 512, "scratch layout");
+
+// The scratch memory.  In host code this name is only a stand-in for the
+// device symbol: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_label_scratch[kScratchBytes];
+
+xy_status fail(xy_status s, const char *fmt, ...) {
+  char msg[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof(msg), fmt, ap);
+  va_end(ap);
+  xy_set_last_error_message(msg);  // read back through xy_last_error()
+  return s;
+}
+
+// device address of the scratch, looked up once per device
+constexpr int kMaxDevices = 64;
+unsigned char *g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_setup_mutex;
+
+xy_status scratch_for_current_device(unsigned char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(XY_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(XY_EUNSUPPORTED, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_label_scratch);
+    if (e != cudaSuccess)
+      return fail(XY_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return XY_OK;
+}
+
+// Write the descriptor, the work prefix and a zeroed state word into the
+// scratch (values travel as kernel arguments, so no host buffer must outlive
+// the call).
+__global__ void k_static_setup(LatDesc d, LatDesc *d_desc, uint32_t *d_prefix) {
+  *d_desc = d;
+  d_prefix[0] = 0u;
+  d_prefix[1] = d.ntiles;
+  *d.st = DevState{};  // error word (and everything else) starts at zero
+}
+
+// Pack byte bonds into the tile-major bit planes: one warp per tile row.
+__global__ void k_static_pack(const uint8_t *__restrict__ right,
+                              const uint8_t *__restrict__ down, LatDesc d) {
+  const uint64_t gw = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint64_t rows = static_cast<uint64_t>(d.ntiles) * kStaticTile;
+  if (gw >= rows) return;
+  const uint32_t tile = static_cast<uint32_t>(gw / kStaticTile);
+  const uint32_t r = static_cast<uint32_t>(gw % kStaticTile);
+  const Tile g = tile_geom<kStaticTile>(d.L, d.ntx, tile);
+  bool br = false, bd = false;
+  if (r < g.h && lane < static_cast<int>(g.w)) {
+    const uint64_t i = static_cast<uint64_t>(g.y0 + r) * d.L + g.x0 + lane;
+    br = right[i] != 0;
+    bd = down[i] != 0;
+  }
+  const uint32_t R = __ballot_sync(0xFFFFFFFFu, br);
+  const uint32_t D = __ballot_sync(0xFFFFFFFFu, bd);
+  if (lane == 0) {
+    d.rplane[gw] = R;
+    d.dplane[gw] = D;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_t *d_down,
+                                uint32_t *d_labels, void *cuda_stream, int sync) {
+  if (L < 2 || L > XY_STATIC_MAX_L)
+    return fail(XY_EINVAL, "L = %u outside 2..%u (the size of the built-in scratch)", L,
+                XY_STATIC_MAX_L);
+  if (!d_right || !d_down || !d_labels) return fail(XY_EINVAL, "NULL device pointer");
+  unsigned char *scratch = nullptr;
+  xy_status s = scratch_for_current_device(&scratch);
+  if (s != XY_OK) return s;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+  LatDesc d{};
+  d.L = L;
+  d.ntx = (L + 31) / 32;
+  d.nty = (L + kStaticTile - 1) / kStaticTile;
+  d.ntiles = d.ntx * d.nty;
+  d.label = d_labels;
+  d.rplane = reinterpret_cast<uint32_t *>(scratch + kOffRplane);
+  d.dplane = reinterpret_cast<uint32_t *>(scratch + kOffDplane);
+  d.st = reinterpret_cast<DevState *>(scratch + kOffState);
+  LatDesc *d_desc = reinterpret_cast<LatDesc *>(scratch + kOffDesc);
+  uint32_t *d_prefix = reinterpret_cast<uint32_t *>(scratch + kOffPrefix);
+  const uint32_t nw = d.ntiles;
+
+  k_static_setup<<<1, 1, 0, stream>>>(d, d_desc, d_prefix);
+  const uint64_t rows = static_cast<uint64_t>(nw) * kStaticTile;
+  k_static_pack<<<static_cast<uint32_t>((rows * 32 + 255) / 256), 256, 0, stream>>>(d_right,
+                                                                                  d_down, d);
+  k_bond_label<kStaticTile, float, true, true>
+      <<<nw, kThreads, bond_label_smem<kStaticTile>(), stream>>>(d_desc, d_prefix, 1, nw);
+  const uint64_t items = static_cast<uint64_t>(nw) * (kStaticTile + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  k_merge<kStaticTile><<<eb, kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
+  k_compress<kStaticTile><<<eb, kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
+  k_flip_measure<kStaticTile, float, true>
+      <<<nw, kThreads, flip_smem<kStaticTile>(), stream>>>(d_desc, d_prefix, 1, nw);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(XY_ECUDA, "launch: %s", cudaGetErrorString(e));
+  if (!sync) return XY_OK;
+  e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return fail(XY_ECUDA, "synchronize: %s", cudaGetErrorString(e));
+  uint32_t err = 0;
+  e = cudaMemcpy(&err, &d.st->err, sizeof(err), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(XY_ECUDA, "error word: %s", cudaGetErrorString(e));
+  if (err) return fail(XY_ETIMEOUT, "device-side find/union loop hit its bound (err=%#x)", err);
+  return XY_OK;
+}
+
+}  // extern "C"
