@@ -285,86 +285,96 @@ __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
 }
 
 // ---------------------------------------------------------------------------
-// Tile union-find over bond words already in shared memory (sR, sD).
-// Row runs come from the right-bond word by bit scans; vertical unions are
-// issued only at the first column of each pair of vertically touching runs.
-// Writes tile-local labels (global index of the tile minimum) to `label`.
+// K1 layout: a CTA owns one 32 x TY tile; warp w owns the band of B = TY/8
+// consecutive rows starting at r0 = w*B, lane = column.  Projections stay in
+// registers (the right neighbour by shuffle, the row below from the next
+// iteration).  Labels come from a row scan inside the band: each row run
+// takes the smallest root among the runs above it that it touches (a
+// segmented minimum over the run's lanes), and only a run that touches two
+// different upper components causes a union.  Bands are then joined across
+// their boundary rows, and every site gets the root of its run.
+//
+// Union-find nodes are tile-local indices r*32 + c of run starts; par[] lives
+// in shared memory and every link points to a smaller index, so the root of a
+// component is its smallest site, which is also its smallest global index.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kNoRoot = 0xFFFFFFFFu;
+
+// lanes of the run containing `lane`: [start, end]
+__device__ __forceinline__ uint32_t run_start_of(uint32_t starts, int lane) {
+  return 31u - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
+}
+
+// One row of the band scan.  up = the scan root above this lane if the
+// vertical bond from the previous row is active, else kNoRoot.  The run's
+// root is the smallest `up` over its lanes (or its own start node when no
+// lane is connected above), found by a segmented suffix minimum.  Every other
+// upper root that the run touches is an equivalence, appended to the warp's
+// pair list (warp-aggregated, no atomics) and united later by all threads at
+// once; only a full list falls back to an immediate union.  Returns the
+// lane's scan root.
+template <int CAP>
+__device__ __forceinline__ uint32_t scan_row(uint32_t *par, uint32_t *pairs,
+                                             uint32_t &npairs, uint32_t r,
+                                             uint32_t starts, uint32_t up,
+                                             int lane) {
+  const uint32_t s = run_start_of(starts, lane);
+  const uint32_t above = lane == 31 ? 0u : (starts & (0xFFFFFFFEu << lane));
+  const uint32_t e = above ? static_cast<uint32_t>(__ffs(above)) - 2u : 31u;
+  uint32_t m = up;
+#pragma unroll
+  for (int dl = 1; dl < 32; dl <<= 1) {
+    const uint32_t v = __shfl_down_sync(0xFFFFFFFFu, m, dl);
+    if (static_cast<uint32_t>(lane) + dl <= e) m = min(m, v);
+  }
+  // m_run <= up on every lane of the run, so need implies m_run != kNoRoot
+  const uint32_t m_run = __shfl_sync(0xFFFFFFFFu, m, s);
+  const uint32_t node = r * 32u + s;
+  const uint32_t root = (m_run == kNoRoot) ? node : m_run;
+  const uint32_t prev_up = __shfl_up_sync(0xFFFFFFFFu, up, 1);
+  const bool need = up != kNoRoot && up != m_run &&
+                    !(static_cast<uint32_t>(lane) > s && prev_up == up);
+  const uint32_t mask = __ballot_sync(0xFFFFFFFFu, need);
+  if (mask) {
+    const uint32_t off = npairs + __popc(mask & ((1u << lane) - 1u));
+    if (need) {
+      if (off < static_cast<uint32_t>(CAP)) pairs[off] = (up << 16) | m_run;
+      else sunion(par, up, m_run);
+    }
+    npairs += __popc(mask);
+  }
+  if (static_cast<uint32_t>(lane) == s) par[node] = root;
+  __syncwarp();  // the run node is read by other lanes from the next row on
+  return root;
+}
+
+// capacity of a warp's equivalence-pair list
 template <int TY>
-__device__ __forceinline__ void tile_label(const Tile &g, uint32_t L,
-                                           const uint32_t *sR,
-                                           const uint32_t *sD, uint32_t *par,
-                                           uint32_t *label) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rmask = (g.w >= 32u) ? 0x7FFFFFFFu : ((1u << (g.w - 1u)) - 1u);
-  const bool col_ok = lane < static_cast<int>(g.w);
-  // every site points at the start of its row run; run starts are roots
-  for (uint32_t r = warp; r < g.h; r += kWarps) {
-    if (col_ok) {
-      const uint32_t starts = ~((sR[r] & rmask) << 1);
-      const uint32_t s = 31u - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
-      par[r * 32u + lane] = r * 32u + s;
-    }
-  }
-  __syncthreads();
-  // Vertical unions, merged hierarchically: at span s, row blocks
-  // [2ks, 2ks + s) and [2ks + s, 2ks + 2s) join across their boundary row
-  // pair only.  Boundaries of one level touch disjoint node sets, and a
-  // node is at most one link per level from its block root, so trees stay
-  // log2(TY) deep.  One union per pair of vertically touching runs (the
-  // first column where they touch).
-  for (uint32_t span = 1; span < g.h; span <<= 1) {
-    const uint32_t nb = (g.h - span + 2u * span - 1u) / (2u * span);
-    for (uint32_t b = warp; b < nb; b += kWarps) {
-      const uint32_t r = b * 2u * span + span - 1u;
-      if (r + 1u < g.h) {
-        const uint32_t D = sD[r];
-        const uint32_t V = D & ~((D & sR[r] & sR[r + 1] & rmask) << 1);
-        if (col_ok && ((V >> lane) & 1u))
-          sunion(par, r * 32u + lane, (r + 1u) * 32u + lane);
-      }
-    }
-    __syncthreads();
-  }
-  // run starts point straight at their root; every other site is then two
-  // hops from it (all ancestors of a site are run starts)
-  for (uint32_t r = warp; r < g.h; r += kWarps) {
-    const uint32_t starts = ~((sR[r] & rmask) << 1);
-    if (col_ok && ((starts >> lane) & 1u)) {
-      const uint32_t node = r * 32u + lane;
-      par[node] = sfind(par, node);
-    }
-  }
-  __syncthreads();
-  for (uint32_t r = warp; r < g.h; r += kWarps) {
-    if (col_ok) {
-      const uint32_t root = par[par[r * 32u + lane]];
-      label[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] =
-          (g.y0 + (root >> 5)) * L + g.x0 + (root & 31u);
-    }
-  }
+__host__ __device__ constexpr int pair_cap() {
+  return 16 * (TY / kWarps);
 }
 
 template <int TY>
 constexpr size_t bond_label_smem() {
-  return sizeof(float) * (TY + 1) * 33 + sizeof(uint32_t) * (TY * 32 + 2 * TY);
+  return sizeof(uint32_t) * (TY * 32 + 2 * TY + kWarps * pair_cap<TY>());
 }
 
 // ---------------------------------------------------------------------------
 // K1: projection + bonds + coins + tile labels
 // ---------------------------------------------------------------------------
 template <int TY, typename AT, bool EXACT, bool FROM_PLANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     k_bond_label(const LatDesc *__restrict__ descs,
                  const uint32_t *__restrict__ prefix, uint32_t nrep,
                  uint32_t nwork) {
+  constexpr int B = TY / kWarps;  // rows per band
   extern __shared__ __align__(16) unsigned char smem[];
-  float(*sa)[33] = reinterpret_cast<float(*)[33]>(smem);
-  uint32_t *par =
-      reinterpret_cast<uint32_t *>(smem + sizeof(float) * (TY + 1) * 33);
+  uint32_t *par = reinterpret_cast<uint32_t *>(smem);
   uint32_t *sR = par + TY * 32;
   uint32_t *sD = sR + TY;
+  constexpr int CAP = pair_cap<TY>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t *pairs = sD + TY + warp * CAP;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
     const uint32_t rep = find_rep(prefix, nrep, work);
@@ -373,69 +383,82 @@ __global__ void __launch_bounds__(kThreads)
     const uint32_t L = d.L;
     const Tile g = tile_geom<TY>(L, d.ntx, tile);
     DevState *st = d.st;
+    uint32_t npairs = 0u;
+    const uint32_t r0 = static_cast<uint32_t>(warp) * B;
+    const uint32_t nb = r0 < g.h ? min(static_cast<uint32_t>(B), g.h - r0) : 0u;
+    const bool col_ok = lane < static_cast<int>(g.w);
+    const uint32_t rmask = (g.w >= 32u) ? 0x7FFFFFFFu : ((1u << (g.w - 1u)) - 1u);
+    const uint64_t tbase = static_cast<uint64_t>(tile) * TY;
 
+    uint32_t lab_prev = kNoRoot, D_prev = 0u;
+    uint32_t labs[B];
     if (!FROM_PLANES) {
       const uint32_t t = st->t;
       const AT *th = static_cast<const AT *>(d.theta[st->cur]);
       const float cphi = st->cphi32, sphi = st->sphi32;
-      // projections of the tile plus its right column and bottom row; all
-      // loads of a thread are issued before the first use
-      // (thread t < h also loads row t of the column right of the tile)
-      constexpr int KR = TY / kWarps + 1;
-      float tv[KR];
+      const float b2 = st->beta2_32, eps = st->eps;
+      // angles of the band, of the row below it, and (lane k < nb) of row k
+      // of the column right of the tile; all loads issued up front
+      float tv[B + 1];
 #pragma unroll
-      for (int k = 0; k < KR; ++k) {
-        const uint32_t r = warp + k * kWarps;
+      for (int k = 0; k <= B; ++k) {
         tv[k] = 0.0f;
-        if (r <= g.h && lane < static_cast<int>(g.w)) {
+        if (static_cast<uint32_t>(k) <= nb && col_ok) {
+          const uint32_t r = r0 + k;
           const uint64_t row = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L;
           tv[k] = load_angle(th, row + g.x0 + lane);
         }
       }
-      const bool hc = threadIdx.x < g.h;
-      float thc = 0.0f;
-      if (hc) thc = load_angle(th, static_cast<uint64_t>(g.y0 + threadIdx.x) * L + g.xh);
+      float tc = 0.0f;
+      if (static_cast<uint32_t>(lane) < nb)
+        tc = load_angle(th, static_cast<uint64_t>(g.y0 + r0 + lane) * L + g.xh);
+      float a[B + 1];
 #pragma unroll
-      for (int k = 0; k < KR; ++k) {
-        const uint32_t r = warp + k * kWarps;
-        if (r <= g.h && lane < static_cast<int>(g.w)) sa[r][lane] = project32(tv[k], cphi, sphi);
-      }
-      if (hc) sa[threadIdx.x][g.w] = project32(thc, cphi, sphi);
-      __syncthreads();
-      const float b2 = st->beta2_32, eps = st->eps;
-      for (uint32_t r = warp; r < g.h; r += kWarps) {
+      for (int k = 0; k <= B; ++k) a[k] = project32(tv[k], cphi, sphi);
+      const float ac = project32(tc, cphi, sphi);
+
+      // phase A: bonds and coins of every row of the band (rows are
+      // independent here, so their Philox chains overlap)
+      uint32_t Rws[B], Dws[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        Rws[k] = Dws[k] = 0u;
+        if (static_cast<uint32_t>(k) >= nb) continue;  // warp-uniform
+        const uint32_t r = r0 + k;
         const uint32_t gy = g.y0 + r;
+        const float a_c = __shfl_sync(0xFFFFFFFFu, ac, k);
+        float a_r = __shfl_down_sync(0xFFFFFFFFu, a[k], 1);
+        if (static_cast<uint32_t>(lane) + 1u == g.w) a_r = a_c;
         bool br = false, bd = false, cn = false;
-        if (lane < static_cast<int>(g.w)) {
+        if (col_ok) {
           const uint32_t i = gy * L + g.x0 + lane;
           const Words4 rn = philox4x32_10(i, 0u, t, kDomBond, d.key0, d.key1);
-          const float ai = sa[r][lane];
-          const float u0 = fmaf(static_cast<float>(rn.w0), 0x1p-32f, 0x1p-33f);
-          const float u1 = fmaf(static_cast<float>(rn.w1), 0x1p-32f, 0x1p-33f);
-          const float xr = ai * sa[r][lane + 1];
-          const float xd = ai * sa[r + 1][lane];
+          // uniforms from the top 23 bits without an int->float conversion:
+          // 1.m - (1 - 2^-24) is exact and is the centre of the word's 2^-23
+          // bin, i.e. within 2^-24 of the FP64 uniform (w + 1/2) 2^-32
+          const float u0 = __uint_as_float(0x3F800000u | (rn.w0 >> 9)) - 0.99999994f;
+          const float u1 = __uint_as_float(0x3F800000u | (rn.w1 >> 9)) - 0.99999994f;
+          const float xr = a[k] * a_r;
+          const float xd = a[k] * a[k + 1];
           const float pr = xr > 0.0f ? 1.0f - __expf(-b2 * xr) : 0.0f;
           const float pd = xd > 0.0f ? 1.0f - __expf(-b2 * xd) : 0.0f;
           br = u0 < pr;
           bd = u1 < pd;
           if (EXACT) {
-            const bool amb_r = fabsf(u0 - pr) <= eps;
-            const bool amb_d = fabsf(u1 - pd) <= eps;
+            const bool amb_r = fabsf(u0 - pr) <= eps, amb_d = fabsf(u1 - pd) <= eps;
             if (amb_r || amb_d) {
-              const double beta = st->beta, cp = st->cphi, sp = st->sphi;
-              const float thi = load_angle(th, static_cast<uint64_t>(i));
               if (amb_r) {
-                const uint32_t xn = (static_cast<uint32_t>(lane) + 1u < g.w) ? g.x0 + lane + 1u : g.xh;
-                const float thj = load_angle(th, static_cast<uint64_t>(gy) * L + xn);
-                const bool e = bond_fp64(thi, thj, rn.w0, beta, cp, sp);
+                // right neighbour's stored angle (reloaded: this path is rare)
+                const float th_r = (static_cast<uint32_t>(lane) + 1u == g.w)
+                                       ? load_angle(th, static_cast<uint64_t>(gy) * L + g.xh)
+                                       : load_angle(th, static_cast<uint64_t>(i) + 1u);
+                const bool e = bond_fp64(tv[k], th_r, rn.w0, st->beta, st->cphi, st->sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != br) atomicAdd(&st->n_fp32_wrong, 1ull);
                 br = e;
               }
               if (amb_d) {
-                const uint32_t yn = (r + 1u < g.h) ? gy + 1u : g.yh;
-                const float thj = load_angle(th, static_cast<uint64_t>(yn) * L + g.x0 + lane);
-                const bool e = bond_fp64(thi, thj, rn.w1, beta, cp, sp);
+                const bool e = bond_fp64(tv[k], tv[k + 1], rn.w1, st->beta, st->cphi, st->sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != bd) atomicAdd(&st->n_fp32_wrong, 1ull);
                 bd = e;
@@ -447,11 +470,15 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t Rw = __ballot_sync(0xFFFFFFFFu, br);
         const uint32_t Dw = __ballot_sync(0xFFFFFFFFu, bd);
         const uint32_t Cw = __ballot_sync(0xFFFFFFFFu, cn);
+        Rws[k] = Rw;
+        Dws[k] = Dw;
         if (lane == 0) {
+          d.rplane[tbase + r] = Rw;
           sR[r] = Rw;
+        } else if (lane == 1) {
+          d.dplane[tbase + r] = Dw;
           sD[r] = Dw;
-          d.rplane[static_cast<uint64_t>(tile) * TY + r] = Rw;
-          d.dplane[static_cast<uint64_t>(tile) * TY + r] = Dw;
+        } else if (lane == 2) {
           const uint32_t i0 = gy * L + g.x0;
           if (!d.ragged) {
             d.coin[i0 >> 5] = Cw;
@@ -462,14 +489,61 @@ __global__ void __launch_bounds__(kThreads)
           }
         }
       }
+      // phase B: the row scan of the band
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        if (static_cast<uint32_t>(k) >= nb) break;
+        const uint32_t up = (k > 0 && ((D_prev >> lane) & 1u)) ? lab_prev : kNoRoot;
+        lab_prev = scan_row<CAP>(par, pairs, npairs, r0 + k, ~((Rws[k] & rmask) << 1), up, lane);
+        labs[k] = lab_prev;
+        D_prev = Dws[k];
+      }
     } else {
-      for (uint32_t r = threadIdx.x; r < g.h; r += kThreads) {
-        sR[r] = d.rplane[static_cast<uint64_t>(tile) * TY + r];
-        sD[r] = d.dplane[static_cast<uint64_t>(tile) * TY + r];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        if (static_cast<uint32_t>(k) >= nb) break;
+        const uint32_t r = r0 + k;
+        const uint32_t Rw = __ldg(d.rplane + tbase + r);
+        const uint32_t Dw = __ldg(d.dplane + tbase + r);
+        if (lane == 0) {
+          sR[r] = Rw;
+          sD[r] = Dw;
+        }
+        const uint32_t up = (k > 0 && ((D_prev >> lane) & 1u)) ? lab_prev : kNoRoot;
+        lab_prev = scan_row<CAP>(par, pairs, npairs, r, ~((Rw & rmask) << 1), up, lane);
+        labs[k] = lab_prev;
+        D_prev = Dw;
       }
     }
     __syncthreads();
-    tile_label<TY>(g, L, sR, sD, par, d.label);
+    // all threads at once: the warp's recorded equivalences, and the join of
+    // each band to the one above it across their boundary rows
+    const uint32_t np = min(npairs, static_cast<uint32_t>(CAP));
+    for (uint32_t e = lane; e < np; e += 32u) {
+      const uint32_t pr = pairs[e];
+      sunion(par, pr >> 16, pr & 0xFFFFu);
+    }
+    if (warp > 0 && nb > 0) {
+      const uint32_t r = r0 - 1u;
+      const uint32_t D = sD[r];
+      const uint32_t Ra = sR[r] & rmask, Rb = sR[r0] & rmask;
+      const uint32_t V = D & ~((D & Ra & Rb) << 1);
+      if (col_ok && ((V >> lane) & 1u))
+        sunion(par, r * 32u + run_start_of(~(Ra << 1), lane),
+               r0 * 32u + run_start_of(~(Rb << 1), lane));
+    }
+    __syncthreads();
+    // every site: root of its run's root as recorded by the scan
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (static_cast<uint32_t>(k) >= nb) break;
+      const uint32_t r = r0 + k;
+      if (col_ok) {
+        const uint32_t root = sfind(par, labs[k]);
+        d.label[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] =
+            (g.y0 + (root >> 5)) * L + g.x0 + (root & 31u);
+      }
+    }
     __syncthreads();
   }
 }
@@ -595,21 +669,22 @@ __device__ __forceinline__ int fix22(float v) {
 
 template <int TY>
 constexpr size_t flip_smem() {
-  return sizeof(float2) * (TY + 1) * 33;
+  return 0;
 }
 
+// K4 layout: as K1, warp w owns rows r0 .. r0+B-1 of the tile (lane =
+// column) and also resolves the row below its band (the next band's first
+// row, or the row below the tile) and, with lanes 0..B-1, the column right of
+// the tile.  Labels of a row are resolved in batched rounds: the entry of each
+// site's tile root, then (when that root was merged) one confirming load.
 template <int TY, typename AT, bool LABELS_ONLY>
 __global__ void __launch_bounds__(kThreads)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
                    uint32_t nwork) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2(*cs)[33] = reinterpret_cast<float2(*)[33]>(smem);
+  constexpr int B = TY / kWarps;
   __shared__ long long red[kWarps][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // a thread handles rows r = warp + 8k (k < KR, r <= h): column `lane` of
-  // the tile (and of the row below it), and lane 0 also column xh of rows < h
-  constexpr int KR = TY / kWarps + 1;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
     const uint32_t rep = find_rep(prefix, nrep, work);
@@ -623,103 +698,108 @@ __global__ void __launch_bounds__(kThreads)
     const AT *thin = static_cast<const AT *>(d.theta[cur]);
     AT *thout = static_cast<AT *>(d.theta[cur ^ 1u]);
     uint32_t *lab = d.label;
+    const uint32_t r0 = static_cast<uint32_t>(warp) * B;
+    const uint32_t nb = r0 < g.h ? min(static_cast<uint32_t>(B), g.h - r0) : 0u;
     const bool col_ok = lane < static_cast<int>(g.w);
+    const bool vc = static_cast<uint32_t>(lane) < nb;  // column xh, row r0+lane
+    const uint64_t ic = static_cast<uint64_t>(g.y0 + r0 + lane) * L + g.xh;
 
-    // round 1: labels and angles.  Positions of this thread: rows
-    // r = warp + 8k (k < KR, r <= h) at column `lane`, and -- for threads
-    // t < h -- row t of the column right of the tile (xh).
-    uint32_t l0[KR];
-    float t0[KR];
-    bool v0[KR];
-    const bool vh = threadIdx.x < g.h;
-    const uint64_t ih = static_cast<uint64_t>(g.y0 + threadIdx.x) * L + g.xh;
-    uint32_t lh = 0u;
-    float th_h = 0.0f;
+    // round 1: labels and angles of rows r0 .. r0+nb and of column xh
+    uint32_t l[B + 1];
+    float t[B + 1];
 #pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      const uint32_t r = warp + k * kWarps;
-      v0[k] = (r <= g.h) && col_ok;
-      const uint64_t row = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L;
-      l0[k] = 0u;
-      t0[k] = 0.0f;
-      if (v0[k]) {
-        l0[k] = __ldcg(lab + row + g.x0 + lane);
-        if (!LABELS_ONLY) t0[k] = load_angle(thin, row + g.x0 + lane);
+    for (int k = 0; k <= B; ++k) {
+      l[k] = 0u;
+      t[k] = 0.0f;
+      if (static_cast<uint32_t>(k) <= nb && col_ok) {
+        const uint32_t r = r0 + k;
+        const uint64_t i = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L + g.x0 + lane;
+        l[k] = __ldcg(lab + i);
+        if (!LABELS_ONLY) t[k] = load_angle(thin, i);
       }
     }
-    if (vh) {
-      lh = __ldcg(lab + ih);
-      if (!LABELS_ONLY) th_h = load_angle(thin, ih);
+    uint32_t lc = 0u;
+    float tc = 0.0f;
+    if (vc) {
+      lc = __ldcg(lab + ic);
+      if (!LABELS_ONLY) tc = load_angle(thin, ic);
     }
-    // round 2: one more hop (the tile root's entry)
-    uint32_t p0[KR];
+    // round 2: the tile root's entry
+    uint32_t p[B + 1];
 #pragma unroll
-    for (int k = 0; k < KR; ++k) p0[k] = v0[k] ? __ldcg(lab + l0[k]) : 0u;
-    const uint32_t ph = vh ? __ldcg(lab + lh) : 0u;
-    // round 3: where the tile root was merged, confirm the next node is the
-    // root (the usual case after k_compress) or finish the find
+    for (int k = 0; k <= B; ++k)
+      p[k] = (static_cast<uint32_t>(k) <= nb && col_ok) ? __ldcg(lab + l[k]) : 0u;
+    const uint32_t pc = vc ? __ldcg(lab + lc) : 0u;
+    // round 3: where the tile root was merged, confirm that the next node is
+    // the root (the usual case after k_compress) or finish the find
 #pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      if (v0[k] && p0[k] != l0[k]) {
-        const uint32_t q = __ldcg(lab + p0[k]);
-        l0[k] = (q == p0[k]) ? q : gfind_ro(lab, q, st);
+    for (int k = 0; k <= B; ++k) {
+      if (static_cast<uint32_t>(k) <= nb && col_ok && p[k] != l[k]) {
+        const uint32_t q = __ldcg(lab + p[k]);
+        l[k] = (q == p[k]) ? q : gfind_ro(lab, q, st);
       }
     }
-    if (vh && ph != lh) {
-      const uint32_t q = __ldcg(lab + ph);
-      lh = (q == ph) ? q : gfind_ro(lab, q, st);
+    if (vc && pc != lc) {
+      const uint32_t q = __ldcg(lab + pc);
+      lc = (q == pc) ? q : gfind_ro(lab, q, st);
     }
-    // l0 / lh now hold the roots; own sites get their canonical label
+    // canonical labels of the band's own sites
 #pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      const uint32_t r = warp + k * kWarps;
-      if (v0[k] && r < g.h)
-        __stcg(lab + static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane, l0[k]);
+    for (int k = 0; k < B; ++k) {
+      if (static_cast<uint32_t>(k) < nb && col_ok)
+        __stcg(lab + static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane, l[k]);
     }
     if (LABELS_ONLY) continue;
     // round 4: coins of the roots
-    uint32_t f0[KR];
+    uint32_t f[B + 1];
 #pragma unroll
-    for (int k = 0; k < KR; ++k)
-      f0[k] = v0[k] ? (__ldg(d.coin + (l0[k] >> 5)) >> (l0[k] & 31u)) & 1u : 0u;
-    const uint32_t fh = vh ? (__ldg(d.coin + (lh >> 5)) >> (lh & 31u)) & 1u : 0u;
-    // flip, store, and cos/sin of the new angles into shared memory
+    for (int k = 0; k <= B; ++k)
+      f[k] = (static_cast<uint32_t>(k) <= nb && col_ok)
+                 ? (__ldg(d.coin + (l[k] >> 5)) >> (l[k] & 31u)) & 1u
+                 : 0u;
+    const uint32_t fc = vc ? (__ldg(d.coin + (lc >> 5)) >> (lc & 31u)) & 1u : 0u;
+    // reflection, stores, and cos/sin of the new angles
+    float co[B + 1], sn[B + 1];
 #pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      const uint32_t r = warp + k * kWarps;
-      if (v0[k]) {
-        float nv = t0[k];
-        if (f0[k]) {
-          const AT sv = store_value<AT>(wrap_angle(__fadd_rn(c32, -t0[k])));
-          nv = stored_float<AT>(sv);
-          if (r < g.h) thout[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] = sv;
-        } else if (r < g.h) {
-          thout[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] = store_value<AT>(t0[k]);
-        }
-        float s, co;
-        sincosf(nv, &s, &co);
-        cs[r][lane] = make_float2(co, s);
+    for (int k = 0; k <= B; ++k) {
+      float nv = t[k];
+      if (f[k]) {
+        const AT sv = store_value<AT>(wrap_angle(__fadd_rn(c32, -t[k])));
+        nv = stored_float<AT>(sv);
+        if (static_cast<uint32_t>(k) < nb && col_ok)
+          thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = sv;
+      } else if (static_cast<uint32_t>(k) < nb && col_ok) {
+        thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_value<AT>(t[k]);
       }
+      sincosf(nv, &sn[k], &co[k]);
     }
-    if (vh) {
-      float nv = th_h;
-      if (fh) nv = stored_float<AT>(store_value<AT>(wrap_angle(__fadd_rn(c32, -th_h))));
-      float s, co;
-      sincosf(nv, &s, &co);
-      cs[threadIdx.x][g.w] = make_float2(co, s);
+    float cc, sc;
+    {
+      float nv = tc;
+      if (fc) nv = stored_float<AT>(store_value<AT>(wrap_angle(__fadd_rn(c32, -tc))));
+      sincosf(nv, &sc, &cc);
     }
-    __syncthreads();
-    // terms of the tile's own sites
+    // observable terms of the band's own sites
     int acc[6] = {0, 0, 0, 0, 0, 0};
-    if (col_ok) {
-      for (uint32_t r = warp; r < g.h; r += kWarps) {
-        const float2 a = cs[r][lane], rr = cs[r][lane + 1], dd = cs[r + 1][lane];
-        acc[0] += fix22(a.x);
-        acc[1] += fix22(a.y);
-        acc[2] += fix22(fmaf(a.x, rr.x, a.y * rr.y));
-        acc[3] += fix22(fmaf(a.y, rr.x, -(a.x * rr.y)));
-        acc[4] += fix22(fmaf(a.x, dd.x, a.y * dd.y));
-        acc[5] += fix22(fmaf(a.y, dd.x, -(a.x * dd.y)));
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (static_cast<uint32_t>(k) >= nb) break;  // warp-uniform
+      const float cxh = __shfl_sync(0xFFFFFFFFu, cc, k);
+      const float sxh = __shfl_sync(0xFFFFFFFFu, sc, k);
+      float cr = __shfl_down_sync(0xFFFFFFFFu, co[k], 1);
+      float sr = __shfl_down_sync(0xFFFFFFFFu, sn[k], 1);
+      if (static_cast<uint32_t>(lane) + 1u == g.w) {
+        cr = cxh;
+        sr = sxh;
+      }
+      if (col_ok) {
+        const float ci = co[k], si = sn[k], cd = co[k + 1], sd = sn[k + 1];
+        acc[0] += fix22(ci);
+        acc[1] += fix22(si);
+        acc[2] += fix22(fmaf(ci, cr, si * sr));
+        acc[3] += fix22(fmaf(si, cr, -(ci * sr)));
+        acc[4] += fix22(fmaf(ci, cd, si * sd));
+        acc[5] += fix22(fmaf(si, cd, -(ci * sd)));
       }
     }
     long long v[6];
