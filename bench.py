@@ -24,6 +24,8 @@ import sys
 import time
 from pathlib import Path
 
+import numpy as np
+
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
@@ -210,6 +212,10 @@ def run_ours(args):
             out["exact_mode"] = exact_report(xy, L, beta, args)
         if args.big and ws == 1:
             out["l65536"] = run_big(xy, args)
+        if args.batched:
+            out["batched"] = run_batched(xy, args)
+        if args.precision:
+            out["precision"] = run_precision(xy, args)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out), flush=True)
@@ -302,6 +308,99 @@ def run_big(xy, args):
     return out
 
 
+def _event_time(fn, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_batched(xy, args):
+    """256 independent replicas (L from {64..2048}, beta ~ U[1.0, 1.3]) advanced
+    by one launch per kernel per sweep for all of them (CUDA graph replay),
+    tile autotuned per table; against the same replicas run one at a time."""
+    import torch
+
+    import synth
+    from paper_1210_6116_b300 import autotune
+
+    table = synth.replica_table(args.replicas, seed=3)
+    n_sites = sum(r["L"] ** 2 for r in table)
+    out = {"replicas": len(table), "sizes": "L uniform over {64,128,256,512,1024,2048}",
+           "beta": "uniform [1.0, 1.3]", "sites_per_step": n_sites, "sweeps": args.batch_sweeps}
+    stream = torch.cuda.current_stream()
+    for dtype in ("f32", "f16"):
+        ty, times = autotune.best_tile_table(table, dtype=dtype, sweeps=3, use_cache=False)
+        eng = xy.Engine(len(table), dtype=dtype, tile_y=ty)
+        slots = [eng.admit(eng.config(r["L"], r["beta"], r["seed"])) for r in table]
+        eng.step(3)
+        t = _event_time(lambda: eng.step(args.batch_sweeps), stream)
+        e_mean = float(np.mean([eng.measure(s_)[-1]["energy_per_site"] for s_ in slots]))
+        out[dtype] = {"tile": f"32x{ty}", "autotune_ms_per_step": {str(k): round(v, 4) for k, v in times.items()},
+                      "replica_sweeps_per_s": round(len(table) * args.batch_sweeps / t, 1),
+                      "updates_per_ns": round(n_sites * args.batch_sweeps / (t * 1e9), 3),
+                      "ms_per_step": round(t * 1e3 / args.batch_sweeps, 4),
+                      "mean_final_energy_per_site": round(e_mean, 6)}
+        eng.close()
+        del eng
+        torch.cuda.empty_cache()
+    # per-request loop: the same replicas, one lattice at a time
+    n_base = args.batch_base_sweeps
+    total = 0.0
+    lats = []
+    for r in table:
+        lat = xy.Lattice(r["L"], r["beta"], r["seed"], tile_y=32 if r["L"] <= 256 else 64)
+        lat.sweep(2)
+        total += _event_time(lambda: lat.sweep(n_base), stream)
+        lat.close()
+    out["per_request_loop"] = {"replica_sweeps_per_s": round(len(table) * n_base / total, 1),
+                               "updates_per_ns": round(n_sites * n_base / (total * 1e9), 3),
+                               "sweeps_per_replica": n_base, "dtype": "f32"}
+    out["speedup_vs_loop_f32"] = round(out["f32"]["replica_sweeps_per_s"]
+                                       / out["per_request_loop"]["replica_sweeps_per_s"], 2)
+    return out
+
+
+def run_precision(xy, args):
+    """Observable shift of FP32 thresholds and FP16 angle storage against the
+    exact (FP64-threshold) mode on the same seeds, and the FP32 bond mismatch
+    rate measured by exact mode."""
+    import numpy as np
+
+    L, beta, n = args.prec_L, 1.12, args.prec_sweeps
+    res = {}
+    for name, kw in (("exact_f32", dict(exact=True)), ("thr_f32", dict(exact=False)),
+                     ("thr_f32_f16", dict(exact=False, dtype="f16"))):
+        lat = xy.Lattice(L, beta, 2024, **kw)
+        lat.sweep(200)
+        lat.measure()
+        lat.sweep(n)
+        r = lat.measure()
+        if name == "exact_f32":
+            n64, wrong = lat.band_stats()
+            res["fp32_bond_mismatch_rate"] = wrong / (2.0 * L * L * (n + 200))
+        lat.close()
+        stats = {}
+        for f, x in (("energy_per_site", r["energy_per_site"]), ("m2", r["m2"]),
+                     ("beta_upsilon", r["beta"] * r["upsilon"])):
+            nb = 20
+            blocks = x[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
+            stats[f] = (float(blocks.mean()), float(blocks.std(ddof=1) / np.sqrt(nb)))
+        res[name] = {f: {"mean": round(m, 6), "err": round(e, 6)} for f, (m, e) in stats.items()}
+    for name in ("thr_f32", "thr_f32_f16"):
+        res[name]["shift_vs_exact"] = {
+            f: round(res[name][f]["mean"] - res["exact_f32"][f]["mean"], 6)
+            for f in ("energy_per_site", "m2", "beta_upsilon")}
+    res["config"] = f"L={L}, beta={beta}, {n} sweeps after 200, binned errors (20 bins)"
+    return res
+
+
 def cpu_baseline(args):
     """The oracle as it stands, single-threaded, on a bounded sample."""
     import numpy as np
@@ -368,6 +467,13 @@ def main():
     ap.add_argument("--cpu-sweeps", dest="cpu_sweeps", type=int, default=3)
     ap.add_argument("--big-steps", dest="big_steps", type=int, default=10)
     ap.add_argument("--no-big", dest="big", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-precision", dest="precision", action="store_false")
+    ap.add_argument("--replicas", type=int, default=256)
+    ap.add_argument("--batch-sweeps", dest="batch_sweeps", type=int, default=500)
+    ap.add_argument("--batch-base-sweeps", dest="batch_base_sweeps", type=int, default=100)
+    ap.add_argument("--prec-L", dest="prec_L", type=int, default=256)
+    ap.add_argument("--prec-sweeps", dest="prec_sweeps", type=int, default=4000)
     ap.add_argument("--no-cpu", dest="no_cpu", action="store_true")
     ap.add_argument("--no-exact-report", dest="exact_report", action="store_false")
     args = ap.parse_args()

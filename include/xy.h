@@ -205,6 +205,44 @@ xy_status xy_profile(xy_lattice *h, int enable);
 /* Synchronise and return the totals since profiling was enabled. */
 xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out);
 
+/* ---- engine: many lattices stepped by shared launches -------------------- */
+/* Independent replicas or requests (the paper's runs at several L and beta,
+ * Secs. 2-3) advance together: one sweep of every active lattice is one
+ * launch of each sweep kernel over all their tiles, replayed from a CUDA
+ * graph that is re-recorded only when the active set changes.  Each lattice
+ * keeps its own workspace (xy_workspace_size bytes, owned by the caller), its
+ * own random numbers and its own fixed-point observable sums, so its results
+ * are the same whether it runs alone or with others.  Lattices join
+ * (xy_engine_admit) and leave (xy_engine_retire) between steps. */
+typedef struct xy_engine xy_engine;
+/* Device bytes of the engine's own table for up to max_slots lattices. */
+xy_status xy_engine_workspace_size(uint32_t max_slots, size_t *bytes);
+/* angle_dtype, threshold_mode and tile_y (16/32/64/128) are shared by all
+ * lattices of an engine.  Work is enqueued on cuda_stream; the engine also
+ * creates one private stream, used only to record its graph. */
+xy_status xy_engine_create(uint32_t max_slots, int angle_dtype,
+                           int threshold_mode, uint32_t tile_y,
+                           void *d_workspace, size_t bytes, void *cuda_stream,
+                           xy_engine **out);
+/* Add a lattice (L divisible by 32, else XY_EUNSUPPORTED) in its own
+ * workspace; pcc = NULL runs fixed beta, otherwise the PCC rule of
+ * xy_pcc_params after each sweep.  cfg->tile_y is ignored (the engine's is
+ * used).  *slot receives its slot; XY_ENOMEM when all slots are in use. */
+xy_status xy_engine_admit(xy_engine *e, const xy_config *cfg,
+                          const xy_pcc_params *pcc, void *d_workspace,
+                          size_t bytes, uint32_t *slot);
+/* Remove a lattice; its workspace may be reused once this returns. */
+xy_status xy_engine_retire(xy_engine *e, uint32_t slot);
+/* Enqueue n_sweeps sweeps of every active lattice. */
+xy_status xy_engine_step(xy_engine *e, uint32_t n_sweeps);
+/* As xy_measure (sync = 1) for one lattice of the engine. */
+xy_status xy_engine_measure(xy_engine *e, uint32_t slot, xy_obs *out,
+                            uint32_t max_records, uint32_t *n_out);
+xy_status xy_engine_get_angles(xy_engine *e, uint32_t slot, void *host_dst);
+xy_status xy_engine_get_state(xy_engine *e, uint32_t slot, double *beta,
+                              uint64_t *sweep);
+xy_status xy_engine_destroy(xy_engine *e);
+
 /* ---- labeling without any device allocation ------------------------------ */
 /* The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory and therefore cannot provide the workspace

@@ -34,6 +34,9 @@ EXPORTS = (
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
     "xy_get_bonds", "xy_get_labels", "xy_label_bonds", "xy_get_band_stats", "xy_save",
     "xy_load", "xy_run_host", "xy_profile", "xy_profile_read", "xy_label_bonds_static",
+    "xy_engine_workspace_size", "xy_engine_create", "xy_engine_admit", "xy_engine_retire",
+    "xy_engine_step", "xy_engine_measure", "xy_engine_get_angles", "xy_engine_get_state",
+    "xy_engine_destroy",
 )
 KERNEL_NAMES = ("bond_label", "merge", "compress", "flip_measure", "finalize")
 
@@ -105,6 +108,15 @@ def load_library() -> ctypes.CDLL:
         "xy_profile": (I, [P, I]),
         "xy_profile_read": (I, [P, P]),
         "xy_label_bonds_static": (I, [U32, P, P, P, P, I]),
+        "xy_engine_workspace_size": (I, [U32, P]),
+        "xy_engine_create": (I, [U32, I, I, U32, P, ctypes.c_size_t, P, P]),
+        "xy_engine_admit": (I, [P, P, P, P, ctypes.c_size_t, P]),
+        "xy_engine_retire": (I, [P, U32]),
+        "xy_engine_step": (I, [P, U32]),
+        "xy_engine_measure": (I, [P, U32, P, U32, P]),
+        "xy_engine_get_angles": (I, [P, U32, P]),
+        "xy_engine_get_state": (I, [P, U32, P, P]),
+        "xy_engine_destroy": (I, [P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -293,6 +305,96 @@ class Lattice:
     def close(self):
         if getattr(self, "handle", None):
             xy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Engine:
+    """Many lattices advanced by shared launches (xy_engine_* of the C ABI).
+
+    Every admitted lattice gets its own torch workspace; the engine's table
+    lives in one more.  All lattices share dtype, threshold mode and tile."""
+
+    def __init__(self, max_slots: int, *, dtype: str = "f32", exact: bool = False,
+                 tile_y: int = 64, stream=None):
+        import torch
+
+        self.dtype = dtype
+        self.np_dtype = np.float32 if dtype == "f32" else np.float16
+        self.exact = exact
+        self.tile_y = tile_y
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        n = ctypes.c_size_t(0)
+        _check(load_library().xy_engine_workspace_size(max_slots, ctypes.byref(n)))
+        self.table = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        self.handle = ctypes.c_void_p()
+        _check(load_library().xy_engine_create(
+            max_slots, XY_F32 if dtype == "f32" else XY_F16,
+            XY_THR_F64 if exact else XY_THR_F32, tile_y,
+            ctypes.c_void_p(self.table.data_ptr()), n.value,
+            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.handle)))
+        self.workspaces = {}
+        self.L = {}
+
+    def config(self, L: int, beta: float, seed: int, start: str = "random",
+               record_cap: int = 0) -> xy_config:
+        return xy_config(L=L, tile_y=self.tile_y, seed=seed, beta=beta,
+                         angle_dtype=XY_F32 if self.dtype == "f32" else XY_F16,
+                         threshold_mode=XY_THR_F64 if self.exact else XY_THR_F32,
+                         start=0 if start == "random" else 1, record_cap=record_cap)
+
+    @staticmethod
+    def footprint(cfg: xy_config) -> int:
+        return xy_workspace_size(cfg)
+
+    def admit(self, cfg: xy_config, pcc: xy_pcc_params | None = None) -> int:
+        import torch
+
+        nbytes = xy_workspace_size(cfg)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        slot = ctypes.c_uint32(0)
+        _check(load_library().xy_engine_admit(
+            self.handle, ctypes.byref(cfg), ctypes.byref(pcc) if pcc is not None else None,
+            ctypes.c_void_p(ws.data_ptr()), nbytes, ctypes.byref(slot)))
+        self.workspaces[slot.value] = ws
+        self.L[slot.value] = cfg.L
+        return slot.value
+
+    def retire(self, slot: int):
+        _check(load_library().xy_engine_retire(self.handle, slot))
+        self.workspaces.pop(slot, None)
+        self.L.pop(slot, None)
+
+    def step(self, n: int = 1):
+        _check(load_library().xy_engine_step(self.handle, n))
+
+    def measure(self, slot: int, max_records: int = 1 << 20) -> np.ndarray:
+        out = np.zeros(max_records, OBS_DTYPE)
+        n = ctypes.c_uint32(0)
+        _check(load_library().xy_engine_measure(self.handle, slot, _ptr(out), max_records,
+                                                ctypes.byref(n)))
+        return out[: n.value]
+
+    def get_angles(self, slot: int) -> np.ndarray:
+        out = np.zeros(self.L[slot] ** 2, self.np_dtype)
+        _check(load_library().xy_engine_get_angles(self.handle, slot, _ptr(out)))
+        return out
+
+    def state(self, slot: int):
+        b = ctypes.c_double(0)
+        t = ctypes.c_uint64(0)
+        _check(load_library().xy_engine_get_state(self.handle, slot, ctypes.byref(b),
+                                                  ctypes.byref(t)))
+        return b.value, t.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load_library().xy_engine_destroy(self.handle))
             self.handle = None
 
     def __del__(self):

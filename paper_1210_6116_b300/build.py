@@ -34,7 +34,8 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
            "-Xcompiler", "-fPIC", "-diag-suppress", "128",
            "-I", str(ROOT / "include"),
-           str(SRC / "xy_api.cu"), str(SRC / "xy_static.cu"), "-o", str(tmp)]
+           str(SRC / "xy_api.cu"), str(SRC / "xy_engine.cu"),
+           str(SRC / "xy_static.cu"), "-o", str(tmp)]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/xy.h"
+#include "layout.cuh"
 #include "sweep_kernels.cuh"
 
 using namespace xyk;
@@ -39,66 +40,6 @@ xy_status fail(xy_status s, const char *fmt, ...) {
     if (e_ != cudaSuccess)                                                  \
       return fail(XY_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-uint32_t default_tile_y(uint32_t L) {
-  if (L <= 32) return 16;
-  if (L <= 256) return 32;
-  return 64;
-}
-
-bool tile_ok(uint32_t ty) { return ty == 16 || ty == 32 || ty == 64 || ty == 128; }
-
-struct Layout {
-  uint32_t L, TY, ntx, nty, ntiles, rec_cap;
-  size_t esize;
-  size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0,
-      off_theta1, off_label, off_rplane, off_dplane, off_coin, total;
-};
-
-xy_status make_layout(const xy_config *c, Layout *lo) {
-  if (!c) return fail(XY_EINVAL, "config is NULL");
-  if (c->L < 2 || c->L > 65536)
-    return fail(XY_EINVAL, "L = %u outside 2..65536", c->L);
-  if (!(c->beta >= 0.0) || !std::isfinite(c->beta))
-    return fail(XY_EINVAL, "beta must be finite and >= 0");
-  if (c->angle_dtype != XY_F32 && c->angle_dtype != XY_F16)
-    return fail(XY_EINVAL, "angle_dtype must be XY_F32 or XY_F16");
-  if (c->threshold_mode != XY_THR_F32 && c->threshold_mode != XY_THR_F64)
-    return fail(XY_EINVAL, "threshold_mode must be XY_THR_F32 or XY_THR_F64");
-  if (c->start != 0 && c->start != 1)
-    return fail(XY_EINVAL, "start must be 0 (random) or 1 (ordered)");
-  const uint32_t ty = c->tile_y ? c->tile_y : default_tile_y(c->L);
-  if (!tile_ok(ty)) return fail(XY_EINVAL, "tile_y must be 16, 32, 64 or 128");
-  lo->L = c->L;
-  lo->TY = ty;
-  lo->ntx = (c->L + 31) / 32;
-  lo->nty = (c->L + ty - 1) / ty;
-  lo->ntiles = lo->ntx * lo->nty;
-  lo->rec_cap = c->record_cap ? c->record_cap : 4096;
-  lo->esize = c->angle_dtype == XY_F32 ? 4 : 2;
-  const uint64_t n = static_cast<uint64_t>(c->L) * c->L;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    const size_t o = off;
-    off = align_up(off + bytes, 256);
-    return o;
-  };
-  lo->off_state = take(sizeof(DevState));
-  lo->off_desc = take(sizeof(LatDesc));
-  lo->off_prefix = take(2 * sizeof(uint32_t));
-  lo->off_acc = take(sizeof(long long) * kSlots * kAccStride);
-  lo->off_rec = take(sizeof(ObsRecord) * lo->rec_cap);
-  lo->off_theta0 = take(n * lo->esize);
-  lo->off_theta1 = take(n * lo->esize);
-  lo->off_label = take(n * sizeof(uint32_t));
-  lo->off_rplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
-  lo->off_dplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
-  lo->off_coin = take((n / 32 + 2) * sizeof(uint32_t));
-  lo->total = off;
-  return XY_OK;
-}
 
 }  // namespace
 
@@ -297,24 +238,8 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
     delete h;
     return fail(XY_ECUDA, "no CUDA device");
   }
+  h->desc = make_desc(cfg, lo, h->ws);
   LatDesc &d = h->desc;
-  d.L = lo.L;
-  d.ntx = lo.ntx;
-  d.nty = lo.nty;
-  d.ntiles = lo.ntiles;
-  d.key0 = static_cast<uint32_t>(cfg->seed & 0xFFFFFFFFu);
-  d.key1 = static_cast<uint32_t>(cfg->seed >> 32);
-  d.rec_cap = lo.rec_cap;
-  d.ragged = (lo.L % 32) != 0;
-  d.theta[0] = h->ws + lo.off_theta0;
-  d.theta[1] = h->ws + lo.off_theta1;
-  d.label = reinterpret_cast<uint32_t *>(h->ws + lo.off_label);
-  d.rplane = reinterpret_cast<uint32_t *>(h->ws + lo.off_rplane);
-  d.dplane = reinterpret_cast<uint32_t *>(h->ws + lo.off_dplane);
-  d.coin = reinterpret_cast<uint32_t *>(h->ws + lo.off_coin);
-  d.acc = reinterpret_cast<long long *>(h->ws + lo.off_acc);
-  d.st = reinterpret_cast<DevState *>(h->ws + lo.off_state);
-  d.rec = reinterpret_cast<ObsRecord *>(h->ws + lo.off_rec);
   h->d_desc = reinterpret_cast<LatDesc *>(h->ws + lo.off_desc);
   h->d_prefix = reinterpret_cast<uint32_t *>(h->ws + lo.off_prefix);
   h->d_state = d.st;

@@ -1,0 +1,92 @@
+"""Engine (many lattices, shared launches): every lattice's results are the
+same bit for bit as when it runs alone through the single-lattice API, for
+fixed beta and PCC, FP32 and FP16, with lattices joining and leaving between
+steps.  One engine lattice is also checked against the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1210_6116_b300 as xy  # noqa: E402
+from paper_1210_6116_b300 import build as xybuild  # noqa: E402
+
+xybuild.build()
+
+
+def _alone(L, beta, seed, n, *, dtype="f32", exact=False, tile_y=32, pcc=None, start="random"):
+    lat = xy.Lattice(L, beta, seed, dtype=dtype, exact=exact, tile_y=tile_y, start=start)
+    if pcc is None:
+        lat.sweep(n)
+    else:
+        lat.pcc_step(n, target=pcc.target, dbeta0=pcc.dbeta0, halve_every=pcc.halve_every,
+                     block=pcc.block)
+    return lat.measure(), lat.get_angles()
+
+
+@pytest.mark.parametrize("dtype,exact", [("f32", False), ("f32", True), ("f16", False)])
+def test_mixed_batch_equals_alone(dtype, exact):
+    table = synth.replica_table(12, seed=5, sizes=(64, 128, 256, 512), beta_range=(1.0, 1.3))
+    eng = xy.Engine(len(table), dtype=dtype, exact=exact, tile_y=32)
+    slots = [eng.admit(eng.config(r["L"], r["beta"], r["seed"])) for r in table]
+    eng.step(25)
+    for r, s in zip(table, slots):
+        recs, ang = _alone(r["L"], r["beta"], r["seed"], 25, dtype=dtype, exact=exact)
+        np.testing.assert_array_equal(eng.measure(s), recs)
+        np.testing.assert_array_equal(eng.get_angles(s).view(np.uint8), ang.view(np.uint8))
+
+
+def test_admission_and_retirement_between_steps():
+    eng = xy.Engine(4, tile_y=32)
+    a = eng.admit(eng.config(128, 1.1, 11))
+    eng.step(10)
+    b = eng.admit(eng.config(64, 1.2, 12))   # joins late
+    eng.step(10)
+    eng.retire(a)                              # leaves early (20 sweeps)
+    c = eng.admit(eng.config(256, 1.05, 13))  # reuses a's slot
+    eng.step(15)
+    rb = eng.measure(b)
+    rc = eng.measure(c)
+    assert len(rb) == 25 and len(rc) == 15
+    np.testing.assert_array_equal(rb, _alone(64, 1.2, 12, 25)[0])
+    np.testing.assert_array_equal(rc, _alone(256, 1.05, 13, 15)[0])
+    assert eng.state(b)[1] == 25
+
+
+def test_pcc_in_engine_equals_alone():
+    pcc = xy.xy_pcc_params(target=2 / math.pi, dbeta0=0.01, halve_every=500, block=1)
+    eng = xy.Engine(3, tile_y=32)
+    slots = [eng.admit(eng.config(L, 1.0, 40 + L), pcc) for L in (64, 128, 256)]
+    eng.step(60)
+    for L, s in zip((64, 128, 256), slots):
+        recs, ang = _alone(L, 1.0, 40 + L, 60, pcc=pcc)
+        np.testing.assert_array_equal(eng.measure(s), recs)
+        np.testing.assert_array_equal(eng.get_angles(s), ang)
+
+
+def test_engine_lattice_matches_oracle(orc):
+    eng = xy.Engine(2, exact=True, tile_y=32)
+    s0 = eng.admit(eng.config(96, 1.12, 77))
+    eng.admit(eng.config(64, 1.3, 78))
+    eng.step(20)
+    th = orc.init_angles(96, 77, 0)
+    orc.sw_run(th, 96, 96, 1.12, 77, 0, 20, record=False)
+    np.testing.assert_array_equal(eng.get_angles(s0), th)
+
+
+def test_engine_rejects_bad_lattices():
+    eng = xy.Engine(1, tile_y=32)
+    with pytest.raises(xy.XyError) as e:
+        eng.admit(eng.config(100, 1.0, 1))  # L not divisible by 32
+    assert e.value.status == xy.XY_EUNSUPPORTED
+    eng.admit(eng.config(64, 1.0, 1))
+    with pytest.raises(xy.XyError) as e:
+        eng.admit(eng.config(64, 1.0, 2))   # no free slot
+    assert e.value.status == xy.XY_ENOMEM
