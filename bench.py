@@ -216,6 +216,8 @@ def run_ours(args):
             out["batched"] = run_batched(xy, args)
         if args.precision:
             out["precision"] = run_precision(xy, args)
+        if args.serving:
+            out["serving"] = run_serving(xy, args)
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out), flush=True)
@@ -367,6 +369,28 @@ def run_batched(xy, args):
     return out
 
 
+def run_serving(xy, args):
+    """Poisson stream of PCC requests (finite, seeded): continuous batching in
+    the engine against the plain one-at-a-time loop on the same trace."""
+    import synth
+    from paper_1210_6116_b300.serve import Request, Server, run_loop
+
+    trace = [Request(k, r["arrival"], r["L"], r["budget"], r["seed"])
+             for k, r in enumerate(synth.request_trace(args.requests, args.rate, seed=4))]
+    out = {"trace": f"{len(trace)} requests, Poisson rate {args.rate}/s, L log-uniform over "
+                    "{128..8192} (powers of 2), budget uniform 500..5000 sweeps, PCC from "
+                    "beta=1.0, dbeta 0.01 halved every 500 sweeps, target 2/pi",
+           "offered_updates_per_ns": round(sum(r.L * r.L * r.budget for r in trace)
+                                           / (trace[-1].arrival * 1e9), 3)}
+    for policy in ("small-first", "fifo"):
+        srv = Server(max_slots=64, chunk=args.serve_chunk, policy=policy)
+        st = srv.run(trace, realtime=True)
+        srv.close()
+        out[f"server_{policy}"] = st.summary()
+    out["per_request_loop"] = run_loop(trace, realtime=True).summary()
+    return out
+
+
 def run_precision(xy, args):
     """Observable shift of FP32 thresholds and FP16 angle storage against the
     exact (FP64-threshold) mode on the same seeds, and the FP32 bond mismatch
@@ -469,6 +493,10 @@ def main():
     ap.add_argument("--no-big", dest="big", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-precision", dest="precision", action="store_false")
+    ap.add_argument("--no-serving", dest="serving", action="store_false")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--serve-chunk", dest="serve_chunk", type=int, default=100)
     ap.add_argument("--replicas", type=int, default=256)
     ap.add_argument("--batch-sweeps", dest="batch_sweeps", type=int, default=500)
     ap.add_argument("--batch-base-sweeps", dest="batch_base_sweeps", type=int, default=100)
