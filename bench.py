@@ -108,6 +108,20 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate(dist, ws: int, sites_per_step: int, steps: int, t_local: float, device=None):
+    """Whole-job rate over ranks: every rank ran `steps` sweeps of its own
+    lattice; the job takes as long as the slowest rank (max over ranks).
+    dist is torch.distributed (or None for one rank)."""
+    t = t_local
+    if dist is not None and ws > 1:
+        import torch
+
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return ws * sites_per_step * steps / (t * 1e9), t
+
+
 def run_ours(args):
     import torch
 
@@ -153,12 +167,7 @@ def run_ours(args):
     kt = lat.profile_read()
     lat.profile(False)
     recs = lat.measure()
-    t_sec = ms / 1e3
-    if pg:
-        tt = torch.tensor([t_sec], device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_sec = float(tt.item())
-    value = ws * N * args.steps / (t_sec * 1e9)
+    value, t_sec = aggregate(pg, ws, N, args.steps, ms / 1e3, device="cuda")
     ms_per_step = t_sec * 1e3 / args.steps
     launches = 5 * args.steps + math.ceil(args.steps / 1024)
 

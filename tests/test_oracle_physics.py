@@ -261,3 +261,25 @@ def test_pcc_drives_beta_to_the_crossing(orc):
     ml, el = mean_err((lo["beta"] * lo["upsilon"])[200:])
     mh, eh = mean_err((hi["beta"] * hi["upsilon"])[200:])
     assert ml < target + 2 * el and mh > target - 2 * eh, (bf, ml, el, mh, eh)
+
+
+def test_fp16_flip_is_vector_reflection(orc):
+    """FP16 storage: a flipped angle is the reflection of the stored half
+    angle, rounded to FP16 (within half an FP16 ulp at [4, 8): 2^-9, plus the
+    FP32 step), and unflipped angles keep their bits."""
+    L, seed = 24, 6
+    th0 = synth.angles(L * L, seed=12, dtype=np.float16)
+    for t in range(4):
+        phi, c, s, C64, C32 = orc.axis(seed, t)
+        right, down, _ = orc.bonds(th0, L, L, 1.0, seed, t)
+        lab, _ = orc.label_bfs(right, down, L, L)
+        th = th0.copy()
+        fl = orc.flip(th, lab, L, L, seed, t, C32)
+        old = th0.astype(np.float64)
+        proj = np.cos(old) * c + np.sin(old) * s
+        rx, ry = np.cos(old) - 2 * proj * c, np.sin(old) - 2 * proj * s
+        want = np.mod(np.arctan2(ry, rx), 2 * math.pi)
+        d = np.abs(np.angle(np.exp(1j * (th.astype(np.float64) - want))))
+        assert np.all(d[fl == 1] <= 2.0 ** -9 + 1e-6)
+        np.testing.assert_array_equal(th.view(np.uint16)[fl == 0], th0.view(np.uint16)[fl == 0])
+        assert np.all(th.astype(np.float32) < np.float32(2 * math.pi))
