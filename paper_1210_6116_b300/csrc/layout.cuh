@@ -90,6 +90,7 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.key1 = static_cast<uint32_t>(cfg->seed >> 32);
   d.rec_cap = lo.rec_cap;
   d.ragged = (lo.L % 32) != 0;
+  d.Lmagic = ~0ull / lo.L + 1ull;
   d.theta[0] = ws + lo.off_theta0;
   d.theta[1] = ws + lo.off_theta1;
   d.label = reinterpret_cast<uint32_t *>(ws + lo.off_label);

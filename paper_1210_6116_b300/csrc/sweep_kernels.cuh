@@ -80,6 +80,7 @@ struct DevState {
 struct LatDesc {
   uint32_t L, ntx, nty, ntiles;
   uint32_t key0, key1, rec_cap, ragged;
+  uint64_t Lmagic;  // ceil(2^64 / L): x / L == umul64hi(x, Lmagic) for x < 2^32
   void *theta[2];
   uint32_t *label;
   uint32_t *rplane, *dplane;
@@ -315,20 +316,18 @@ __device__ __forceinline__ uint32_t run_start_of(uint32_t starts, int lane) {
 // lane's scan root.
 template <int CAP>
 __device__ __forceinline__ uint32_t scan_row(uint32_t *par, uint32_t *pairs,
-                                             uint32_t &npairs, uint32_t r,
-                                             uint32_t starts, uint32_t up,
-                                             int lane) {
+                                             uint32_t &npairs, uint32_t *runmin,
+                                             uint32_t r, uint32_t starts,
+                                             uint32_t up, int lane) {
   const uint32_t s = run_start_of(starts, lane);
-  const uint32_t above = lane == 31 ? 0u : (starts & (0xFFFFFFFEu << lane));
-  const uint32_t e = above ? static_cast<uint32_t>(__ffs(above)) - 2u : 31u;
-  uint32_t m = up;
-#pragma unroll
-  for (int dl = 1; dl < 32; dl <<= 1) {
-    const uint32_t v = __shfl_down_sync(0xFFFFFFFFu, m, dl);
-    if (static_cast<uint32_t>(lane) + dl <= e) m = min(m, v);
-  }
+  // minimum of `up` over the run, gathered in the run start's slot of the
+  // warp's scratch (every slot holds kNoRoot between rows)
+  if (up != kNoRoot) atomicMin(runmin + s, up);
+  __syncwarp();
   // m_run <= up on every lane of the run, so need implies m_run != kNoRoot
-  const uint32_t m_run = __shfl_sync(0xFFFFFFFFu, m, s);
+  const uint32_t m_run = runmin[s];
+  __syncwarp();
+  if (static_cast<uint32_t>(lane) == s) runmin[s] = kNoRoot;
   const uint32_t node = r * 32u + s;
   const uint32_t root = (m_run == kNoRoot) ? node : m_run;
   const uint32_t prev_up = __shfl_up_sync(0xFFFFFFFFu, up, 1);
@@ -356,7 +355,7 @@ __host__ __device__ constexpr int pair_cap() {
 
 template <int TY>
 constexpr size_t bond_label_smem() {
-  return sizeof(uint32_t) * (TY * 32 + 2 * TY + kWarps * pair_cap<TY>());
+  return sizeof(uint32_t) * (TY * 32 + 2 * TY + kWarps * pair_cap<TY>() + kWarps * 32);
 }
 
 // ---------------------------------------------------------------------------
@@ -375,6 +374,9 @@ __global__ void __launch_bounds__(kThreads, 4)
   constexpr int CAP = pair_cap<TY>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t *pairs = sD + TY + warp * CAP;
+  uint32_t *runmin = sD + TY + kWarps * CAP + warp * 32;
+  runmin[lane] = kNoRoot;
+  __syncwarp();
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
     const uint32_t rep = find_rep(prefix, nrep, work);
@@ -419,10 +421,10 @@ __global__ void __launch_bounds__(kThreads, 4)
 
       // phase A: bonds and coins of every row of the band (rows are
       // independent here, so their Philox chains overlap)
-      uint32_t Rws[B], Dws[B];
+      uint32_t Rws[B], Dws[B], Cws[B];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        Rws[k] = Dws[k] = 0u;
+        Rws[k] = Dws[k] = Cws[k] = 0u;
         if (static_cast<uint32_t>(k) >= nb) continue;  // warp-uniform
         const uint32_t r = r0 + k;
         const uint32_t gy = g.y0 + r;
@@ -467,19 +469,28 @@ __global__ void __launch_bounds__(kThreads, 4)
           }
           cn = (rn.w2 & 1u) != 0u;
         }
-        const uint32_t Rw = __ballot_sync(0xFFFFFFFFu, br);
-        const uint32_t Dw = __ballot_sync(0xFFFFFFFFu, bd);
-        const uint32_t Cw = __ballot_sync(0xFFFFFFFFu, cn);
-        Rws[k] = Rw;
-        Dws[k] = Dw;
-        if (lane == 0) {
+        Rws[k] = __ballot_sync(0xFFFFFFFFu, br);
+        Dws[k] = __ballot_sync(0xFFFFFFFFu, bd);
+        Cws[k] = __ballot_sync(0xFFFFFFFFu, cn);
+      }
+      // one store per plane for the whole band: lane k writes row r0 + k
+      {
+        uint32_t Rw = 0u, Dw = 0u, Cw = 0u;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (lane == k) {
+            Rw = Rws[k];
+            Dw = Dws[k];
+            Cw = Cws[k];
+          }
+        }
+        if (static_cast<uint32_t>(lane) < nb) {
+          const uint32_t r = r0 + lane;
           d.rplane[tbase + r] = Rw;
-          sR[r] = Rw;
-        } else if (lane == 1) {
           d.dplane[tbase + r] = Dw;
+          sR[r] = Rw;
           sD[r] = Dw;
-        } else if (lane == 2) {
-          const uint32_t i0 = gy * L + g.x0;
+          const uint32_t i0 = (g.y0 + r) * L + g.x0;
           if (!d.ragged) {
             d.coin[i0 >> 5] = Cw;
           } else if (Cw) {
@@ -494,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       for (int k = 0; k < B; ++k) {
         if (static_cast<uint32_t>(k) >= nb) break;
         const uint32_t up = (k > 0 && ((D_prev >> lane) & 1u)) ? lab_prev : kNoRoot;
-        lab_prev = scan_row<CAP>(par, pairs, npairs, r0 + k, ~((Rws[k] & rmask) << 1), up, lane);
+        lab_prev = scan_row<CAP>(par, pairs, npairs, runmin, r0 + k, ~((Rws[k] & rmask) << 1), up, lane);
         labs[k] = lab_prev;
         D_prev = Dws[k];
       }
@@ -510,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 4)
           sD[r] = Dw;
         }
         const uint32_t up = (k > 0 && ((D_prev >> lane) & 1u)) ? lab_prev : kNoRoot;
-        lab_prev = scan_row<CAP>(par, pairs, npairs, r, ~((Rw & rmask) << 1), up, lane);
+        lab_prev = scan_row<CAP>(par, pairs, npairs, runmin, r, ~((Rw & rmask) << 1), up, lane);
         labs[k] = lab_prev;
         D_prev = Dw;
       }
@@ -675,8 +686,10 @@ constexpr size_t flip_smem() {
 // K4 layout: as K1, warp w owns rows r0 .. r0+B-1 of the tile (lane =
 // column) and also resolves the row below its band (the next band's first
 // row, or the row below the tile) and, with lanes 0..B-1, the column right of
-// the tile.  Labels of a row are resolved in batched rounds: the entry of each
-// site's tile root, then (when that root was merged) one confirming load.
+// the tile.  Roots come in two batched rounds of loads: a site's entry (its
+// tile root, or its root when k_compress jumped it), then that entry's entry,
+// which k_compress has made the root (every merged tile root is jumped until
+// its parent is a root; an unmerged one is its own entry).
 template <int TY, typename AT, bool LABELS_ONLY>
 __global__ void __launch_bounds__(kThreads)
     k_flip_measure(const LatDesc *__restrict__ descs,
@@ -730,19 +743,12 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = 0; k <= B; ++k)
       p[k] = (static_cast<uint32_t>(k) <= nb && col_ok) ? __ldcg(lab + l[k]) : 0u;
     const uint32_t pc = vc ? __ldcg(lab + lc) : 0u;
-    // round 3: where the tile root was merged, confirm that the next node is
-    // the root (the usual case after k_compress) or finish the find
+    // after k_compress a site's entry is its tile root or its root, and a
+    // tile root's entry is itself or its root: the entry's entry is the root
 #pragma unroll
-    for (int k = 0; k <= B; ++k) {
-      if (static_cast<uint32_t>(k) <= nb && col_ok && p[k] != l[k]) {
-        const uint32_t q = __ldcg(lab + p[k]);
-        l[k] = (q == p[k]) ? q : gfind_ro(lab, q, st);
-      }
-    }
-    if (vc && pc != lc) {
-      const uint32_t q = __ldcg(lab + pc);
-      lc = (q == pc) ? q : gfind_ro(lab, q, st);
-    }
+    for (int k = 0; k <= B; ++k)
+      if (static_cast<uint32_t>(k) <= nb && col_ok) l[k] = p[k];
+    if (vc) lc = pc;
     // canonical labels of the band's own sites
 #pragma unroll
     for (int k = 0; k < B; ++k) {
