@@ -691,7 +691,7 @@ constexpr size_t flip_smem() {
 // which k_compress has made the root (every merged tile root is jumped until
 // its parent is a root; an unmerged one is its own entry).
 template <int TY, typename AT, bool LABELS_ONLY>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
                    uint32_t nwork) {
