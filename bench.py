@@ -44,6 +44,13 @@ M_CANON = 16.5
 M_BUILT = 4.0 + 4.0 + 0.375 + 16.0
 
 
+def _sm_max_mhz():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return float(json.loads(p.read_text()).get("sm_max_mhz", 2032.0))
+    return 2032.0
+
+
 def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -182,6 +189,7 @@ def run_ours(args):
         kernels = {k: {"ms_per_launch": round(v[0] / v[1], 5), "share": round(v[0] / sum(x[0] for x in kt.values()), 4)}
                    for k, v in kt.items()}
         traffic = None
+        alu = None
         tfile = ROOT / "profiles" / "traffic.json"
         if tfile.exists():
             import hashlib
@@ -190,6 +198,16 @@ def run_ours(args):
             same = hashlib.sha256(src.read_bytes()).hexdigest()[:16] == tj.get("kernels_source_sha256_16")
             if same and tj.get("kernel") == dom and tj.get("L") == L:
                 traffic = tj.get("bytes_per_launch")
+                if tj.get("thread_inst_per_launch"):
+                    # instruction issue ceiling: 148 SMs x 4 schedulers x 32 lanes x SM clock
+                    peak_ti = 148 * 4 * 32 * _sm_max_mhz() * 1e6 / 1e12
+                    ach_ti = tj["thread_inst_per_launch"] / (dms * 1e-3) / 1e12
+                    alu = {"bound": "alu", "kernel": dom, "achieved": round(ach_ti, 2),
+                           "peak": round(peak_ti, 2), "unit": "T thread-instructions/s",
+                           "frac": round(ach_ti / peak_ti, 4),
+                           "thread_inst_per_launch": tj["thread_inst_per_launch"],
+                           "how": "executed instructions from the ncu capture in profiles/, "
+                                  "duration from this run's CUDA events"}
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -205,6 +223,7 @@ def run_ours(args):
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "bytes_per_site": KERNEL_BYTES_PER_SITE[dom]},
+            "roofline_alu": alu,
             "sweep_roofline": {"model_canon_B_per_site": M_CANON, "model_built_B_per_site": M_BUILT,
                                "frac_canon": round(value * M_CANON / peak, 4),
                                "frac_built": round(value * M_BUILT / peak, 4)},
