@@ -79,6 +79,9 @@ typedef struct {
                               1: ordered start (all angles 0)               */
   uint32_t record_cap;     /* observable records kept on the device (ring);
                               0 = 4096                                      */
+  uint32_t measure_xi;     /* 1: also record chik (second-moment correlation
+                              length, Eqs. (8)-(9)); 0: chik = 0           */
+  uint32_t reserved;       /* must be 0                                     */
 } xy_config;
 
 /* Observables of the configuration after one sweep (FP64).  N = L*L.
@@ -90,10 +93,17 @@ typedef struct {
  *   upsilon = ex - beta N sx^2   (Eq. (4) with J = 1, T = 1/beta, L^2 = N);
  *             the paper's PCC compares beta*upsilon with its target
  *   beta   = the inverse temperature the sweep ran at
- *   sweep  = the sweep counter t of that sweep (0-based)                  */
+ *   sweep  = the sweep counter t of that sweep (0-based)
+ *   chik   = (|F(k_x)|^2 + |F(k_y)|^2) / (2N), F(k) = sum_r s(r) e^{ik.r} at
+ *            k_x = (2 pi/L, 0), k_y = (0, 2 pi/L): the configuration's
+ *            chi(k) at the smallest wave vector (Eq. (9), read as the
+ *            thermal average of |F|^2).  With chi0 = N m2,
+ *            xi_2nd = sqrt(<chi0>/<chik> - 1) / (2 sin(pi/L))   (Eq. (8)).
+ *            Recorded only when the config sets measure_xi, else 0.    */
 typedef struct {
   double energy_per_site, m2, mx, my, ex, sx, ey, sy, upsilon, beta;
   uint64_t sweep;
+  double chik;
 } xy_obs;
 
 /* Helicity-modulus PCC (Sec. 2): after every `block` sweeps, with

@@ -44,11 +44,12 @@ def build(force: bool = False) -> Path:
 class Sums(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "sum_cos", "sum_sin", "sum_cos_r", "sum_sin_r", "sum_cos_d",
-        "sum_sin_d", "n_sites", "n_links_r", "n_links_d")]
+        "sum_sin_d", "n_sites", "n_links_r", "n_links_d")] + [
+        ("fx", ctypes.c_double * 4), ("fy", ctypes.c_double * 4)]
 
 
 OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy",
-              "upsilon", "beta")
+              "upsilon", "beta", "chik")
 
 
 class Obs(ctypes.Structure):

@@ -408,10 +408,23 @@ static void sums_generic(int Lx, int Ly, int per_x, int per_y,
                          const double *ang, orc_sums *s) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long double c = 0, sn = 0, cr = 0, sr = 0, cd = 0, sd = 0;
+  long double fx[4] = {0, 0, 0, 0}, fy[4] = {0, 0, 0, 0};
   uint64_t nr = 0, nd = 0;
   for (uint64_t i = 0; i < n; ++i) {
-    c += cos(ang[i]);
-    sn += sin(ang[i]);
+    double ci = cos(ang[i]), si = sin(ang[i]);
+    c += ci;
+    sn += si;
+    uint64_t x = i % (uint64_t)Lx, y = i / (uint64_t)Lx;
+    double kx = ORC_TWO_PI * (double)x / (double)Lx;
+    double ky = ORC_TWO_PI * (double)y / (double)Ly;
+    fx[0] += ci * cos(kx);
+    fx[1] += ci * sin(kx);
+    fx[2] += si * cos(kx);
+    fx[3] += si * sin(kx);
+    fy[0] += ci * cos(ky);
+    fy[1] += ci * sin(ky);
+    fy[2] += si * cos(ky);
+    fy[3] += si * sin(ky);
     uint64_t j;
     if (right_of(Lx, Ly, per_x, i, &j)) {
       double d = ang[i] - ang[j];
@@ -435,6 +448,10 @@ static void sums_generic(int Lx, int Ly, int per_x, int per_y,
   s->n_sites = (double)n;
   s->n_links_r = (double)nr;
   s->n_links_d = (double)nd;
+  for (int k = 0; k < 4; ++k) {
+    s->fx[k] = (double)fx[k];
+    s->fy[k] = (double)fy[k];
+  }
 }
 
 void orc_sums_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
@@ -466,6 +483,12 @@ void orc_derive(const orc_sums *s, double beta, orc_obs *o) {
   /* Eq. (4) with J = 1, T = 1/beta and L^2 = N: Upsilon = e - beta N s^2 */
   o->upsilon = o->ex - beta * n * o->sx * o->sx;
   o->beta = beta;
+  double ax = 0.0, ay = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    ax += s->fx[k] * s->fx[k];
+    ay += s->fy[k] * s->fy[k];
+  }
+  o->chik = (ax + ay) / (2.0 * n);
 }
 
 /* ------------------------------------------------------------------------ */

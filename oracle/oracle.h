@@ -58,6 +58,12 @@ typedef struct {
   double n_sites;      /* N = Lx*Ly                             */
   double n_links_r;    /* number of right links (N if periodic) */
   double n_links_d;    /* number of down links                  */
+  /* Fourier components of the spin field at the smallest wave vectors,
+   * k = (2 pi / Lx, 0) and (0, 2 pi / Ly) (the paper's Eq. (9)):
+   * fx[0..3] = sum_r (cos th cos kx, cos th sin kx, sin th cos kx,
+   * sin th sin kx) with kx = 2 pi x / Lx; fy[] the same with y. */
+  double fx[4];
+  double fy[4];
 } orc_sums;
 
 /* Derived per-configuration observables. */
@@ -69,6 +75,9 @@ typedef struct {
   double ey, sy;           /* same along y                                 */
   double upsilon;          /* ex - beta N sx^2 (Eq. 4, J = 1, T = 1/beta)  */
   double beta;             /* the beta the configuration was sampled at    */
+  double chik;             /* (|F(kx)|^2 + |F(ky)|^2) / (2N): the
+                              configuration's chi at the smallest nonzero
+                              wave vector, averaged over x and y (Eq. (9)) */
 } orc_obs;
 
 /* ---- Philox4x32-10 ------------------------------------------------------ */

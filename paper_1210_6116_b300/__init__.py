@@ -51,17 +51,20 @@ class xy_config(ctypes.Structure):
     _fields_ = [("L", ctypes.c_uint32), ("tile_y", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("beta", ctypes.c_double), ("angle_dtype", ctypes.c_int32),
                 ("threshold_mode", ctypes.c_int32), ("start", ctypes.c_int32),
-                ("record_cap", ctypes.c_uint32)]
+                ("record_cap", ctypes.c_uint32), ("measure_xi", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy", "upsilon", "beta")
 
 
 class xy_obs(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in OBS_FIELDS] + [("sweep", ctypes.c_uint64)]
+    _fields_ = ([(n, ctypes.c_double) for n in OBS_FIELDS] + [("sweep", ctypes.c_uint64)]
+                + [("chik", ctypes.c_double)])
 
 
-OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS] + [("sweep", np.uint64)])
+OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS] + [("sweep", np.uint64),
+                                                             ("chik", np.float64)])
 assert OBS_DTYPE.itemsize == ctypes.sizeof(xy_obs)
 
 
@@ -207,7 +210,7 @@ class Lattice:
 
     def __init__(self, L: int, beta: float, seed: int, *, dtype: str = "f32",
                  exact: bool = True, start: str = "random", tile_y: int = 0,
-                 record_cap: int = 0, stream=None):
+                 record_cap: int = 0, measure_xi: bool = False, stream=None):
         import torch  # plumbing: device memory and streams
 
         self.L = int(L)
@@ -216,7 +219,8 @@ class Lattice:
         self.cfg = xy_config(L=self.L, tile_y=tile_y, seed=seed, beta=beta,
                              angle_dtype=XY_F32 if dtype == "f32" else XY_F16,
                              threshold_mode=XY_THR_F64 if exact else XY_THR_F32,
-                             start=0 if start == "random" else 1, record_cap=record_cap)
+                             start=0 if start == "random" else 1, record_cap=record_cap,
+                             measure_xi=1 if measure_xi else 0)
         self.nbytes = xy_workspace_size(self.cfg)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
@@ -342,11 +346,12 @@ class Engine:
         self.L = {}
 
     def config(self, L: int, beta: float, seed: int, start: str = "random",
-               record_cap: int = 0) -> xy_config:
+               record_cap: int = 0, measure_xi: bool = False) -> xy_config:
         return xy_config(L=L, tile_y=self.tile_y, seed=seed, beta=beta,
                          angle_dtype=XY_F32 if self.dtype == "f32" else XY_F16,
                          threshold_mode=XY_THR_F64 if self.exact else XY_THR_F32,
-                         start=0 if start == "random" else 1, record_cap=record_cap)
+                         start=0 if start == "random" else 1, record_cap=record_cap,
+                         measure_xi=1 if measure_xi else 0)
 
     @staticmethod
     def footprint(cfg: xy_config) -> int:

@@ -32,7 +32,7 @@ struct Layout {
   uint32_t L, TY, ntx, nty, ntiles, rec_cap;
   size_t esize;
   size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0,
-      off_theta1, off_label, off_rplane, off_dplane, off_coin, total;
+      off_theta1, off_label, off_rplane, off_dplane, off_coin, off_wave, total;
 };
 
 inline xy_status make_layout(const xy_config *c, Layout *lo) {
@@ -47,6 +47,8 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
     return layout_fail(XY_EINVAL, "threshold_mode must be XY_THR_F32 or XY_THR_F64");
   if (c->start != 0 && c->start != 1)
     return layout_fail(XY_EINVAL, "start must be 0 (random) or 1 (ordered)");
+  if (c->measure_xi > 1 || c->reserved != 0)
+    return layout_fail(XY_EINVAL, "measure_xi must be 0 or 1 and reserved 0");
   const uint32_t ty = c->tile_y ? c->tile_y : default_tile_y(c->L);
   if (!tile_ok(ty)) return layout_fail(XY_EINVAL, "tile_y must be 16, 32, 64 or 128");
   lo->L = c->L;
@@ -74,6 +76,7 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
   lo->off_rplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
   lo->off_dplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
   lo->off_coin = take((n / 32 + 2) * sizeof(uint32_t));
+  lo->off_wave = take(static_cast<size_t>(c->L) * 8);
   lo->total = off;
   return XY_OK;
 }
@@ -97,6 +100,8 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.rplane = reinterpret_cast<uint32_t *>(ws + lo.off_rplane);
   d.dplane = reinterpret_cast<uint32_t *>(ws + lo.off_dplane);
   d.coin = reinterpret_cast<uint32_t *>(ws + lo.off_coin);
+  d.xi = cfg->measure_xi ? 1u : 0u;
+  d.wave = reinterpret_cast<const float2 *>(ws + lo.off_wave);
   d.acc = reinterpret_cast<long long *>(ws + lo.off_acc);
   d.st = reinterpret_cast<DevState *>(ws + lo.off_state);
   d.rec = reinterpret_cast<ObsRecord *>(ws + lo.off_rec);

@@ -39,7 +39,7 @@ namespace xyk {
 constexpr int kThreads = 256;          // 8 warps per tile CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kSlots = 64;             // accumulator slots per lattice
-constexpr int kAccStride = 8;          // int64 per slot (6 used)
+constexpr int kAccStride = 16;         // int64 per slot (6, or 14 with xi)
 constexpr uint32_t kFindCap = 1u << 22;  // bound on any global find / union loop
 
 // error bits recorded in DevState::err
@@ -53,6 +53,7 @@ constexpr double kFixScale = 4194304.0;  // 2^22
 struct ObsRecord {  // identical layout to xy_obs
   double energy_per_site, m2, mx, my, ex, sx, ey, sy, upsilon, beta;
   uint64_t sweep;
+  double chik;
 };
 
 struct DevState {
@@ -81,6 +82,8 @@ struct LatDesc {
   uint32_t L, ntx, nty, ntiles;
   uint32_t key0, key1, rec_cap, ragged;
   uint64_t Lmagic;  // ceil(2^64 / L): x / L == umul64hi(x, Lmagic) for x < 2^32
+  uint32_t xi, pad0;  // 1: accumulate the Fourier sums of chik
+  const float2 *wave;  // [L]: (cos, sin)(2 pi x / L), used when xi
   void *theta[2];
   uint32_t *label;
   uint32_t *rplane, *dplane;
@@ -690,13 +693,13 @@ constexpr size_t flip_smem() {
 // tile root, or its root when k_compress jumped it), then that entry's entry,
 // which k_compress has made the root (every merged tile root is jumped until
 // its parent is a root; an unmerged one is its own entry).
-template <int TY, typename AT, bool LABELS_ONLY>
-__global__ void __launch_bounds__(kThreads, 5)
+template <int TY, typename AT, bool LABELS_ONLY, bool XI = false>
+__global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need registers
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
                    uint32_t nwork) {
   constexpr int B = TY / kWarps;
-  __shared__ long long red[kWarps][6];
+  __shared__ long long red[kWarps][XI ? 14 : 6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
@@ -785,8 +788,17 @@ __global__ void __launch_bounds__(kThreads, 5)
       if (fc) nv = stored_float<AT>(store_value<AT>(wrap_angle(__fadd_rn(c32, -tc))));
       sincosf(nv, &sc, &cc);
     }
-    // observable terms of the band's own sites
-    int acc[6] = {0, 0, 0, 0, 0, 0};
+    // observable terms of the band's own sites (with d.xi also the Fourier
+    // sums of chik: s(r) times (cos, sin)(2 pi x / L) and (2 pi y / L))
+    constexpr int NV = XI ? 14 : 6;
+    int acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0;
+    const bool xi = XI && d.xi != 0u;
+    float2 wx = make_float2(0.0f, 0.0f);
+    if constexpr (XI) {
+      if (xi && col_ok) wx = __ldg(d.wave + g.x0 + lane);
+    }
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       if (static_cast<uint32_t>(k) >= nb) break;  // warp-uniform
@@ -806,22 +818,38 @@ __global__ void __launch_bounds__(kThreads, 5)
         acc[3] += fix22(fmaf(si, cr, -(ci * sr)));
         acc[4] += fix22(fmaf(ci, cd, si * sd));
         acc[5] += fix22(fmaf(si, cd, -(ci * sd)));
+        if constexpr (XI) {
+          if (xi) {
+            const float2 wy = __ldg(d.wave + g.y0 + r0 + k);
+            acc[NV - 8] += fix22(ci * wx.x);
+            acc[NV - 7] += fix22(ci * wx.y);
+            acc[NV - 6] += fix22(si * wx.x);
+            acc[NV - 5] += fix22(si * wx.y);
+            acc[NV - 4] += fix22(ci * wy.x);
+            acc[NV - 3] += fix22(ci * wy.y);
+            acc[NV - 2] += fix22(si * wy.x);
+            acc[NV - 1] += fix22(si * wy.y);
+          }
+        }
       }
     }
-    long long v[6];
+    const int nv = xi ? 14 : 6;
+    long long v[NV];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NV; ++k) {
       v[k] = acc[k];
+      if (k < nv) {
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+        for (int off = 16; off > 0; off >>= 1)
+          v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+      }
     }
     if (lane == 0) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) red[warp][k] = v[k];
+      for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < static_cast<unsigned>(nv)) {
       long long sum = 0;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) sum += red[w][threadIdx.x];
@@ -867,25 +895,27 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
   const LatDesc &d = descs[rep];
   DevState *st = d.st;
   const int lane = threadIdx.x;
-  long long v[6] = {0, 0, 0, 0, 0, 0};
+  long long v[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) v[k] = 0;
   for (int s = lane; s < kSlots; s += 32) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 14; ++k) {
       v[k] += d.acc[s * kAccStride + k];
       d.acc[s * kAccStride + k] = 0;
     }
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 14; ++k) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
       v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
   }
   if (lane != 0) return;
   const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
-  double S[6];
+  double S[14];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) S[k] = static_cast<double>(v[k]) / kFixScale;
+  for (int k = 0; k < 14; ++k) S[k] = static_cast<double>(v[k]) / kFixScale;
   const double beta = st->beta;
   ObsRecord o;
   o.mx = S[0] / n;
@@ -899,6 +929,10 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
   o.upsilon = o.ex - beta * n * o.sx * o.sx;  // Eq. (4), J = 1, T = 1/beta
   o.beta = beta;
   o.sweep = st->t;
+  double f2 = 0.0;
+#pragma unroll
+  for (int k = 6; k < 14; ++k) f2 += S[k] * S[k];
+  o.chik = f2 / (2.0 * n);  // 0 unless the lattice measures xi
   d.rec[st->rec_count % d.rec_cap] = o;
   st->rec_count += 1;
   double nb = beta;
@@ -939,6 +973,15 @@ __global__ void k_init_angles(LatDesc d, int ordered) {
     }
     th[i] = store_value<AT>(v);
   }
+}
+
+// (cos, sin)(2 pi x / L) for the Fourier sums of chik, rounded from FP64
+static __global__ void k_init_wave(LatDesc d) {
+  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.L) return;
+  double s, c;
+  sincospi(2.0 * static_cast<double>(x) / static_cast<double>(d.L), &s, &c);
+  const_cast<float2 *>(d.wave)[x] = make_float2(__double2float_rn(c), __double2float_rn(s));
 }
 
 static __global__ void k_init_state(LatDesc d, double beta) {

@@ -99,8 +99,12 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   if ((e = mark(h)) != cudaSuccess) return e;
   k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   if ((e = mark(h)) != cudaSuccess) return e;
-  k_flip_measure<TY, AT, false>
-      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if (h->desc.xi)
+    k_flip_measure<TY, AT, false, true>
+        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  else
+    k_flip_measure<TY, AT, false, false>
+        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
   if ((e = mark(h)) != cudaSuccess) return e;
   k_finalize<<<1, 32, 0, s>>>(h->d_desc, 1);
   if ((e = mark(h)) != cudaSuccess) return e;
@@ -263,6 +267,7 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
                            h->stream)) != cudaSuccess)
     return bail("coin reset", e);
   k_init_state<<<1, 1, 0, h->stream>>>(d, cfg->beta);
+  k_init_wave<<<(lo.L + 255) / 256, 256, 0, h->stream>>>(d);
   const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;
   const uint32_t blocks = static_cast<uint32_t>(
       std::min<uint64_t>((n + 255) / 256, static_cast<uint64_t>(h->sm_count) * 16));

@@ -57,25 +57,28 @@ struct Slot {
 
 template <int TY, typename AT, bool EXACT>
 void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uint32_t nw,
-                cudaStream_t s) {
+                bool xi, cudaStream_t s) {
   k_bond_label<TY, AT, EXACT, false>
       <<<nw, kThreads, bond_label_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
   k_merge<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
   k_compress<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
-  k_flip_measure<TY, AT, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
+  if (xi)  // some lattice measures xi; the others skip it by their own flag
+    k_flip_measure<TY, AT, false, true><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
+  else
+    k_flip_measure<TY, AT, false, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   k_finalize<<<nrep, 32, 0, s>>>(descs, nrep);
 }
 
 template <typename AT, bool EXACT>
 void launch_ty(uint32_t TY, const LatDesc *descs, const uint32_t *prefix, uint32_t nrep,
-               uint32_t nw, cudaStream_t s) {
+               uint32_t nw, bool xi, cudaStream_t s) {
   switch (TY) {
-    case 16: launch_all<16, AT, EXACT>(descs, prefix, nrep, nw, s); break;
-    case 32: launch_all<32, AT, EXACT>(descs, prefix, nrep, nw, s); break;
-    case 64: launch_all<64, AT, EXACT>(descs, prefix, nrep, nw, s); break;
-    default: launch_all<128, AT, EXACT>(descs, prefix, nrep, nw, s); break;
+    case 16: launch_all<16, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
+    case 32: launch_all<32, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
+    case 64: launch_all<64, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
+    default: launch_all<128, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
   }
 }
 
@@ -105,12 +108,14 @@ size_t table_bytes(uint32_t max_slots) {
 }
 
 void launch_table(xy_engine *e, cudaStream_t s) {
+  bool xi = false;
+  for (const LatDesc &d : e->h_descs) xi = xi || d.xi;
   if (e->dtype == XY_F32) {
-    if (e->thr == XY_THR_F64) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, s);
-    else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, s);
+    if (e->thr == XY_THR_F64) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
   } else {
-    if (e->thr == XY_THR_F64) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, s);
-    else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, s);
+    if (e->thr == XY_THR_F64) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
   }
 }
 
@@ -225,6 +230,7 @@ xy_status xy_engine_admit(xy_engine *e, const xy_config *cfg, const xy_pcc_param
   XY_CUDA(cudaMemsetAsync(s.desc.acc, 0, sizeof(long long) * kSlots * kAccStride, e->stream));
   XY_CUDA(cudaMemsetAsync(s.desc.coin, 0, (static_cast<size_t>(lo.L) * lo.L / 32 + 2) * 4, e->stream));
   k_init_state<<<1, 1, 0, e->stream>>>(s.desc, c.beta);
+  k_init_wave<<<(lo.L + 255) / 256, 256, 0, e->stream>>>(s.desc);
   const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;
   const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((n + 255) / 256, 4096));
   if (c.angle_dtype == XY_F32)

@@ -13,16 +13,26 @@ The north star's "1e-6 relative" holds on top of these wherever the value is
 O(1) (E/site ~ -1.4, e_x ~ 0.7): the test takes max(1e-6 |value|, bound).
 M^2 = mx^2 + my^2 and Upsilon = e_x - beta N s_x^2 inherit the bounds by
 error propagation.
+
+chik (Eq. (9) at the smallest wave vector) is built from eight Fourier sums
+F_c = sum_r {cos, sin}(theta_r) {cos, sin}(2 pi x / L).  Each term is the
+product of an FP32 cos/sin (<= 1.2e-7), a wave factor rounded from FP64 to
+FP32 (<= 6e-8), the product's rounding (<= 6e-8) and the 2^-22 grid
+(<= 1.2e-7): EPS_WAVE = 3.6e-7 per term, so |dF_c| <= dF = EPS_WAVE N.  With
+sum_c |F_c| <= sqrt(8 sum_c F_c^2) = 4 sqrt(N chik), the error of
+chik = sum_c F_c^2 / (2N) is at most (4 dF sqrt(N chik) + 4 dF^2) / N.
 """
 import numpy as np
 
 REL = 1e-6
 EPS_LINK = 6e-7
 EPS_SITE = 2.4e-7
+EPS_WAVE = 3.6e-7
 
 
-def obs_close(g: dict, o: dict, N: int, beta: float):
-    """Return a list of (field, gpu, oracle, tol) that violate the tolerance."""
+def obs_close(g: dict, o: dict, N: int, beta: float, xi: bool = False):
+    """Return a list of (field, gpu, oracle, tol) that violate the tolerance.
+    xi: the GPU lattice measures chik; otherwise its chik must be exactly 0."""
     bad = []
 
     def chk(k, tol):
@@ -40,6 +50,11 @@ def obs_close(g: dict, o: dict, N: int, beta: float):
                   2 * (abs(o["mx"]) + abs(o["my"]) + EPS_SITE) * EPS_SITE))
     chk("upsilon", max(REL * abs(o["upsilon"]),
                        EPS_LINK + beta * N * (2 * abs(o["sx"]) + EPS_LINK) * EPS_LINK))
+    if xi:
+        dF = EPS_WAVE * N
+        chk("chik", max(REL * o["chik"], (4 * dF * np.sqrt(N * o["chik"]) + 4 * dF * dF) / N))
+    elif g.get("chik", 0.0) != 0.0:
+        bad.append(("chik", g["chik"], 0.0, 0.0))
     if g["beta"] != o["beta"]:
         bad.append(("beta", g["beta"], o["beta"], 0.0))
     return bad

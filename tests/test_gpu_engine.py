@@ -21,8 +21,10 @@ from paper_1210_6116_b300 import build as xybuild  # noqa: E402
 xybuild.build()
 
 
-def _alone(L, beta, seed, n, *, dtype="f32", exact=False, tile_y=32, pcc=None, start="random"):
-    lat = xy.Lattice(L, beta, seed, dtype=dtype, exact=exact, tile_y=tile_y, start=start)
+def _alone(L, beta, seed, n, *, dtype="f32", exact=False, tile_y=32, pcc=None, start="random",
+           measure_xi=False):
+    lat = xy.Lattice(L, beta, seed, dtype=dtype, exact=exact, tile_y=tile_y, start=start,
+                     measure_xi=measure_xi)
     if pcc is None:
         lat.sweep(n)
     else:
@@ -41,6 +43,24 @@ def test_mixed_batch_equals_alone(dtype, exact):
         recs, ang = _alone(r["L"], r["beta"], r["seed"], 25, dtype=dtype, exact=exact)
         np.testing.assert_array_equal(eng.measure(s), recs)
         np.testing.assert_array_equal(eng.get_angles(s).view(np.uint8), ang.view(np.uint8))
+
+
+def test_xi_and_plain_lattices_share_launches():
+    """Lattices that record chik and lattices that do not run in one engine
+    (the engine then launches the chik-summing observable kernel for all of
+    them): each equals its alone run, and chik stays 0 where it is off."""
+    table = synth.replica_table(8, seed=9, sizes=(64, 128, 256), beta_range=(1.0, 1.2))
+    eng = xy.Engine(len(table), tile_y=32)
+    xi = [k % 2 == 0 for k in range(len(table))]
+    slots = [eng.admit(eng.config(r["L"], r["beta"], r["seed"], measure_xi=x))
+             for r, x in zip(table, xi)]
+    eng.step(20)
+    for r, s, x in zip(table, slots, xi):
+        recs, ang = _alone(r["L"], r["beta"], r["seed"], 20, measure_xi=x)
+        got = eng.measure(s)
+        np.testing.assert_array_equal(got, recs)
+        np.testing.assert_array_equal(eng.get_angles(s), ang)
+        assert (got["chik"] > 0).all() if x else not got["chik"].any()
 
 
 def test_admission_and_retirement_between_steps():

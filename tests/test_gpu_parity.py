@@ -119,6 +119,24 @@ def test_fp16_chain_bit_exact(orc):
         assert not obs_close(rec_dict(recs[k]), od, L * L, beta)
 
 
+@pytest.mark.parametrize("L,ty,dtype", [(3, 16, "f32"), (64, 32, "f32"), (100, 32, "f32"),
+                                        (257, 64, "f32"), (80, 32, "f16"), (512, 128, "f32")])
+def test_chik_chain_matches_oracle(orc, L, ty, dtype):
+    """chik (Eq. (9) at the smallest wave vector) recorded every sweep of a
+    chain: angles bit-exact, chik within the bound of gpu_helpers."""
+    beta, seed = 1.1, 900 + L
+    lat = _lat(L, beta, seed, tile_y=ty, dtype=dtype, measure_xi=True)
+    th = orc.init_angles(L, seed, 0, dtype=np.float16 if dtype == "f16" else np.float32)
+    lat.sweep(25)
+    recs = lat.measure()
+    o = orc.sw_run(th, L, L, beta, seed, 0, 25)
+    np.testing.assert_array_equal(lat.get_angles().view(np.uint8), th.view(np.uint8))
+    for k in range(25):
+        od = {n: float(o[k][n]) for n in o.dtype.names}
+        bad = obs_close(rec_dict(recs[k]), od, L * L, beta, xi=True)
+        assert not bad, (k, bad)
+
+
 # ------------------------------------------------------------ limits on GPU
 def test_beta_zero_has_no_bonds():
     lat = _lat(64, 0.0, 3)
@@ -261,3 +279,9 @@ def test_bench_size_one_sweep_full_parity(orc):
     orc.flip(th, g_lab, L, L, seed, 0, orc.axis(seed, 0)[4])
     np.testing.assert_array_equal(lat.get_angles(), th)
     assert not obs_close(rec_dict(rec[0]), orc.measure(th, L, L, beta), L * L, beta)
+    # the same sweep with chik recorded: same angles, chik within its bound
+    lat_xi = _lat(L, beta, seed, tile_y=64, measure_xi=True)
+    lat_xi.sweep(1)
+    rec_xi = lat_xi.measure()
+    np.testing.assert_array_equal(lat_xi.get_angles(), th)
+    assert not obs_close(rec_dict(rec_xi[0]), orc.measure(th, L, L, beta), L * L, beta, xi=True)

@@ -283,3 +283,26 @@ def test_fp16_flip_is_vector_reflection(orc):
         assert np.all(d[fl == 1] <= 2.0 ** -9 + 1e-6)
         np.testing.assert_array_equal(th.view(np.uint16)[fl == 0], th0.view(np.uint16)[fl == 0])
         assert np.all(th.astype(np.float32) < np.float32(2 * math.pi))
+
+
+# ------------------------------------------------------------ xi_2nd (Eq. (9))
+@pytest.mark.parametrize("L,k", [(16, 1), (24, 1), (32, 2)])
+def test_chik_plane_waves(orc, L, k):
+    """theta = 2 pi k x / L: s(r) = (cos q x, sin q x).  At the smallest wave
+    vector along x, |F|^2 = N^2/2 when k = 1 (and 0 when k > 1, orthogonal
+    harmonics); along y every column sums to zero.  chik = (|Fx|^2+|Fy|^2)/2N."""
+    N = L * L
+    o = orc.measure(synth.twisted_angles(L, k, axis=0), L, L, 1.0)
+    want = (N * N / 2.0 if k == 1 else 0.0) / (2 * N)
+    assert o["chik"] == pytest.approx(want, abs=1e-6 * N)
+    o = orc.measure(synth.twisted_angles(L, k, axis=1), L, L, 1.0)
+    assert o["chik"] == pytest.approx(want, abs=1e-6 * N)
+
+
+def test_chik_uniform_and_staggered(orc):
+    L = 20
+    assert orc.measure(np.full(L * L, np.float32(0.7)), L, L, 1.0)["chik"] == pytest.approx(0.0, abs=1e-9)
+    # a single flipped site (theta = pi) on an ordered field: F(k) = -2 e^{ik r0}
+    th = np.zeros(L * L, np.float32)
+    th[3 * L + 5] = np.float32(math.pi)
+    assert orc.measure(th, L, L, 1.0)["chik"] == pytest.approx((4 + 4) / (2 * L * L), rel=1e-6)
