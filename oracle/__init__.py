@@ -74,6 +74,13 @@ def lib():
             "orc_philox4x32_10": (None, [_P, _P, _P]),
             "orc_philox_stream": (None, [_U64, _P, _I, _U64, _P]),
             "orc_axis": (None, [_U64, _U32, _P, _P]),
+            "orc_axis_u16": (None, [_U64, _U32, _P, _P]),
+            "orc_init_angles_u16": (None, [_I, _I, _U64, _I, _P]),
+            "orc_bonds_u16": (ctypes.c_long, [_I, _I, _I, _I, _P, _D, _U64, _U32, _P, _P]),
+            "orc_bond_up_u16": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, ctypes.c_int64, _I, _P, _P]),
+            "orc_flip_u16": (ctypes.c_long, [_I, _I, _P, _P, _U64, _U32, ctypes.c_uint16, _P]),
+            "orc_sums_u16": (None, [_I, _I, _I, _I, _P, _P]),
+            "orc_sw_run_u16": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, _U32, _P, _P, _P, _P, _P]),
             "orc_init_angles_f32": (None, [_I, _I, _U64, _I, _P]),
             "orc_init_angles_f16": (None, [_I, _I, _U64, _I, _P]),
             "orc_bonds_f32": (ctypes.c_long, [_I, _I, _I, _I, _P, _D, _U64, _U32, _P, _P]),
@@ -134,11 +141,24 @@ def axis(seed: int, t: int):
     return float(out[0]), float(out[1]), float(out[2]), float(out[3]), np.float32(c32[0])
 
 
+def axis_u16(seed: int, t: int):
+    """(phi_q, cos phi_q, sin phi_q, C64, Cq) of sweep t for u16 angles."""
+    out = np.zeros(4, np.float64)
+    cq = np.zeros(1, np.uint16)
+    lib().orc_axis_u16(seed, t, _ptr(out), _ptr(cq))
+    return float(out[0]), float(out[1]), float(out[2]), float(out[3]), int(cq[0])
+
+
+# Angle arrays: float32 (FP32), float16 (FP16 bits) or uint16 (u16 fixed
+# point, theta = q 2 pi / 65536); every step below dispatches on the dtype.
 def init_angles(L: int, seed: int, start: int, dtype=np.float32, Ly: int | None = None) -> np.ndarray:
     Ly = L if Ly is None else Ly
     if dtype == np.float32:
         th = np.zeros(L * Ly, np.float32)
         lib().orc_init_angles_f32(L, Ly, seed, start, _ptr(th))
+    elif dtype == np.uint16:
+        th = np.zeros(L * Ly, np.uint16)
+        lib().orc_init_angles_u16(L, Ly, seed, start, _ptr(th))
     else:
         th = np.zeros(L * Ly, np.uint16)
         lib().orc_init_angles_f16(L, Ly, seed, start, _ptr(th))
@@ -156,6 +176,9 @@ def bonds(theta: np.ndarray, Lx: int, Ly: int, beta: float, seed: int, t: int,
     if theta.dtype == np.float32:
         band = lib().orc_bonds_f32(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t,
                                    _ptr(right), _ptr(down))
+    elif theta.dtype == np.uint16:
+        band = lib().orc_bonds_u16(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t,
+                                   _ptr(right), _ptr(down))
     else:
         band = lib().orc_bonds_f16(Lx, Ly, per_x, per_y, _ptr(theta.view(np.uint16)), beta,
                                    seed, t, _ptr(right), _ptr(down))
@@ -166,8 +189,8 @@ def bond_up(theta: np.ndarray, Lx: int, Ly: int, beta: float, seed: int, t: int,
             i: int, direction: int, per_x: int = 1, per_y: int = 1):
     u = np.zeros(1, np.float64)
     p = np.zeros(1, np.float64)
-    lib().orc_bond_up_f32(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t, i, direction,
-                          _ptr(u), _ptr(p))
+    f = lib().orc_bond_up_u16 if theta.dtype == np.uint16 else lib().orc_bond_up_f32
+    f(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t, i, direction, _ptr(u), _ptr(p))
     return float(u[0]), float(p[0])
 
 
@@ -193,11 +216,14 @@ def coin(seed: int, t: int, root: int) -> int:
 
 
 def flip(theta: np.ndarray, label: np.ndarray, Lx: int, Ly: int, seed: int, t: int, c32):
-    """Flips theta in place; returns the per-site flip set."""
+    """Flips theta in place; returns the per-site flip set.  c32 is C32 of
+    axis() for FP32/FP16 angles and Cq of axis_u16() for u16 angles."""
     fl = np.zeros(Lx * Ly, np.uint8)
     lab = np.ascontiguousarray(label, np.uint32)
     if theta.dtype == np.float32:
         lib().orc_flip_f32(Lx, Ly, _ptr(theta), _ptr(lab), seed, t, float(c32), _ptr(fl))
+    elif theta.dtype == np.uint16:
+        lib().orc_flip_u16(Lx, Ly, _ptr(theta), _ptr(lab), seed, t, int(c32), _ptr(fl))
     else:
         lib().orc_flip_f16(Lx, Ly, _ptr(theta.view(np.uint16)), _ptr(lab), seed, t, float(c32),
                            _ptr(fl))
@@ -208,6 +234,8 @@ def sums(theta: np.ndarray, Lx: int, Ly: int, per_x: int = 1, per_y: int = 1) ->
     s = Sums()
     if theta.dtype == np.float32:
         lib().orc_sums_f32(Lx, Ly, per_x, per_y, _ptr(theta), ctypes.byref(s))
+    elif theta.dtype == np.uint16:
+        lib().orc_sums_u16(Lx, Ly, per_x, per_y, _ptr(theta), ctypes.byref(s))
     else:
         lib().orc_sums_f16(Lx, Ly, per_x, per_y, _ptr(theta.view(np.uint16)), ctypes.byref(s))
     return s
@@ -248,6 +276,9 @@ def sw_run(theta: np.ndarray, Lx: int, Ly: int, beta: float, seed: int, t0: int,
     optr = _ptr(obs) if record else None
     if theta.dtype == np.float32:
         lib().orc_sw_run_f32(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t0, n,
+                             _ptr(sc.right), _ptr(sc.down), _ptr(sc.label), _ptr(sc.queue), optr)
+    elif theta.dtype == np.uint16:
+        lib().orc_sw_run_u16(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t0, n,
                              _ptr(sc.right), _ptr(sc.down), _ptr(sc.label), _ptr(sc.queue), optr)
     else:
         lib().orc_sw_run_f16(Lx, Ly, per_x, per_y, _ptr(theta.view(np.uint16)), beta, seed, t0,

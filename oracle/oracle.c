@@ -16,6 +16,8 @@
 #define ORC_TWO_PI 6.283185307179586
 #define ORC_PI 3.141592653589793
 #define ORC_TWO_PI_F ((float)6.283185307179586)
+/* u16 angle step 2pi / 65536 (a power-of-two scaling of ORC_TWO_PI: exact) */
+#define ORC_U16_STEP (ORC_TWO_PI / 65536.0)
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11, Sec. 3): ten rounds of two 32x32->64  */
@@ -116,6 +118,29 @@ void orc_axis(uint64_t seed, uint32_t t, double out[4], float *c32) {
   *c32 = cf;
 }
 
+/* The axis of sweep t for u16 fixed-point angles, theta = q 2pi / 65536.
+ * The reflection constant has to lie on the angle grid for the flip to be
+ * the exact integer map q -> (Cq - q) mod 65536, and the bonds have to use
+ * the axis that this map reflects about, or the flipped projection would not
+ * be exactly the negated one.  So the axis is put on the grid: m = the 16
+ * bits of the axis word below its top bit (phi mod pi = pi frac(2u), floored
+ * to the grid), phi_q = pi m / 65536 and Cq = (m + 32768) mod 65536, so that
+ * pi + 2 phi_q = Cq 2pi / 65536 (mod 2pi).  phi_q and phi_q + pi give the
+ * same bonds and the same reflection. */
+void orc_axis_u16(uint64_t seed, uint32_t t, double out[4], uint16_t *cq) {
+  uint32_t w[4];
+  philox_draw(seed, 0u, 0u, t, ORC_DOM_AXIS, w);
+  uint64_t bits = ((uint64_t)w[0] << 32) | (uint64_t)w[1];
+  uint32_t m = (uint32_t)(bits >> 47) & 0xFFFFu;
+  double phi = ORC_PI * ((double)m / 65536.0);
+  uint32_t c = (m + 32768u) & 0xFFFFu;
+  out[0] = phi;
+  out[1] = cos(phi);
+  out[2] = sin(phi);
+  out[3] = (double)c * ORC_U16_STEP;
+  *cq = (uint16_t)c;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Initial angles.                                                           */
 /* ------------------------------------------------------------------------ */
@@ -141,6 +166,20 @@ void orc_init_angles_f16(int Lx, int Ly, uint64_t seed, int start,
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   for (uint64_t i = 0; i < n; ++i)
     theta_bits[i] = store_angle_f16(init_angle(seed, i, start));
+}
+
+/* u16: the top 16 bits of the same INIT word (theta = q 2pi / 65536). */
+void orc_init_angles_u16(int Lx, int Ly, uint64_t seed, int start,
+                         uint16_t *q) {
+  uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
+  for (uint64_t i = 0; i < n; ++i) {
+    q[i] = 0;
+    if (start != 0) continue;
+    uint32_t w[4];
+    philox_draw(seed, (uint32_t)i, (uint32_t)(i >> 32), 0xffffffffu,
+                ORC_DOM_INIT, w);
+    q[i] = (uint16_t)(w[0] >> 16);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -183,14 +222,12 @@ static double uniform_open(uint32_t w) {
   return ((double)w + 0.5) * 0x1.0p-32; /* in (0, 1), exact */
 }
 
-/* Generic bonds over angles already widened to FP64 (ang[i]). */
+/* Generic bonds over angles already widened to FP64 (ang[i]), for the
+ * axis (cphi, sphi) of sweep t. */
 static long bonds_generic(int Lx, int Ly, int per_x, int per_y,
-                          const double *ang, double beta, uint64_t seed,
-                          uint32_t t, uint8_t *right, uint8_t *down) {
-  double ax[4];
-  float c32;
-  orc_axis(seed, t, ax, &c32);
-  double cphi = ax[1], sphi = ax[2];
+                          const double *ang, double cphi, double sphi,
+                          double beta, uint64_t seed, uint32_t t,
+                          uint8_t *right, uint8_t *down) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long band = 0;
   for (uint64_t i = 0; i < n; ++i) {
@@ -230,13 +267,22 @@ static double *widen_f16(const uint16_t *bits, uint64_t n) {
   return ang;
 }
 
+static double *widen_u16(const uint16_t *q, uint64_t n) {
+  double *ang = (double *)malloc(n * sizeof(double));
+  for (uint64_t i = 0; i < n; ++i) ang[i] = (double)q[i] * ORC_U16_STEP;
+  return ang;
+}
+
 long orc_bonds_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
                    double beta, uint64_t seed, uint32_t t, uint8_t *right,
                    uint8_t *down) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
+  double ax[4];
+  float c32;
+  orc_axis(seed, t, ax, &c32);
   double *ang = widen_f32(theta, n);
-  long band = bonds_generic(Lx, Ly, per_x, per_y, ang, beta, seed, t, right,
-                            down);
+  long band = bonds_generic(Lx, Ly, per_x, per_y, ang, ax[1], ax[2], beta,
+                            seed, t, right, down);
   free(ang);
   return band;
 }
@@ -245,19 +291,37 @@ long orc_bonds_f16(int Lx, int Ly, int per_x, int per_y,
                    const uint16_t *theta_bits, double beta, uint64_t seed,
                    uint32_t t, uint8_t *right, uint8_t *down) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
+  double ax[4];
+  float c32;
+  orc_axis(seed, t, ax, &c32);
   double *ang = widen_f16(theta_bits, n);
-  long band = bonds_generic(Lx, Ly, per_x, per_y, ang, beta, seed, t, right,
-                            down);
+  long band = bonds_generic(Lx, Ly, per_x, per_y, ang, ax[1], ax[2], beta,
+                            seed, t, right, down);
   free(ang);
   return band;
 }
 
-void orc_bond_up_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
-                     double beta, uint64_t seed, uint32_t t, int64_t i,
-                     int dir, double *u, double *p) {
+long orc_bonds_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
+                   double beta, uint64_t seed, uint32_t t, uint8_t *right,
+                   uint8_t *down) {
+  uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   double ax[4];
-  float c32;
-  orc_axis(seed, t, ax, &c32);
+  uint16_t cq;
+  orc_axis_u16(seed, t, ax, &cq);
+  double *ang = widen_u16(q, n);
+  long band = bonds_generic(Lx, Ly, per_x, per_y, ang, ax[1], ax[2], beta,
+                            seed, t, right, down);
+  free(ang);
+  return band;
+}
+
+/* u and p of the right (dir 0) or down (dir 1) bond of site i, over angles
+ * widened to FP64 by `angle` and the axis (cphi, sphi) of sweep t. */
+static void bond_up_generic(int Lx, int Ly, int per_x, int per_y,
+                            double (*angle)(const void *, uint64_t),
+                            const void *theta, double cphi, double sphi,
+                            double beta, uint64_t seed, uint32_t t, int64_t i,
+                            int dir, double *u, double *p) {
   uint32_t w[4];
   philox_draw(seed, (uint32_t)i, (uint32_t)((uint64_t)i >> 32), t,
               ORC_DOM_BOND, w);
@@ -267,9 +331,37 @@ void orc_bond_up_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
   *u = uniform_open(dir == 0 ? w[0] : w[1]);
   *p = 0.0;
   if (!ok) return;
-  double ai = projection((double)theta[i], ax[1], ax[2]);
-  double aj = projection((double)theta[j], ax[1], ax[2]);
+  double ai = projection(angle(theta, (uint64_t)i), cphi, sphi);
+  double aj = projection(angle(theta, j), cphi, sphi);
   *p = bond_probability(ai, aj, beta);
+}
+
+static double angle_f32(const void *theta, uint64_t i) {
+  return (double)((const float *)theta)[i];
+}
+
+static double angle_u16(const void *theta, uint64_t i) {
+  return (double)((const uint16_t *)theta)[i] * ORC_U16_STEP;
+}
+
+void orc_bond_up_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
+                     double beta, uint64_t seed, uint32_t t, int64_t i,
+                     int dir, double *u, double *p) {
+  double ax[4];
+  float c32;
+  orc_axis(seed, t, ax, &c32);
+  bond_up_generic(Lx, Ly, per_x, per_y, angle_f32, theta, ax[1], ax[2], beta,
+                  seed, t, i, dir, u, p);
+}
+
+void orc_bond_up_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
+                     double beta, uint64_t seed, uint32_t t, int64_t i,
+                     int dir, double *u, double *p) {
+  double ax[4];
+  uint16_t cq;
+  orc_axis_u16(seed, t, ax, &cq);
+  bond_up_generic(Lx, Ly, per_x, per_y, angle_u16, q, ax[1], ax[2], beta,
+                  seed, t, i, dir, u, p);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -401,6 +493,22 @@ long orc_flip_f16(int Lx, int Ly, uint16_t *theta_bits, const uint32_t *label,
   return count;
 }
 
+/* u16: reflection about the grid axis, q' = (Cq - q) mod 65536, exact. */
+long orc_flip_u16(int Lx, int Ly, uint16_t *q, const uint32_t *label,
+                  uint64_t seed, uint32_t t, uint16_t cq, uint8_t *flipped) {
+  uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
+  long count = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    int f = orc_coin(seed, t, label[i]);
+    if (flipped) flipped[i] = (uint8_t)f;
+    if (f) {
+      q[i] = (uint16_t)(((uint32_t)cq + 65536u - (uint32_t)q[i]) & 0xFFFFu);
+      ++count;
+    }
+  }
+  return count;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Step 5: observables (Eqs. (3)-(6)).  Terms in FP64, sums in long double.  */
 /* ------------------------------------------------------------------------ */
@@ -466,6 +574,14 @@ void orc_sums_f16(int Lx, int Ly, int per_x, int per_y,
                   const uint16_t *theta_bits, orc_sums *s) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   double *ang = widen_f16(theta_bits, n);
+  sums_generic(Lx, Ly, per_x, per_y, ang, s);
+  free(ang);
+}
+
+void orc_sums_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
+                  orc_sums *s) {
+  uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
+  double *ang = widen_u16(q, n);
   sums_generic(Lx, Ly, per_x, per_y, ang, s);
   free(ang);
 }
@@ -545,6 +661,26 @@ void orc_sw_run_f16(int Lx, int Ly, int per_x, int per_y,
     if (obs) {
       orc_sums sm;
       orc_sums_f16(Lx, Ly, per_x, per_y, theta_bits, &sm);
+      orc_derive(&sm, beta, &obs[s]);
+    }
+  }
+}
+
+void orc_sw_run_u16(int Lx, int Ly, int per_x, int per_y, uint16_t *q,
+                    double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                    uint8_t *right, uint8_t *down, uint32_t *label,
+                    uint32_t *queue, orc_obs *obs) {
+  for (uint32_t s = 0; s < n; ++s) {
+    uint32_t t = t0 + s;
+    double ax[4];
+    uint16_t cq;
+    orc_axis_u16(seed, t, ax, &cq);
+    orc_bonds_u16(Lx, Ly, per_x, per_y, q, beta, seed, t, right, down);
+    orc_label_bfs(Lx, Ly, per_x, per_y, right, down, label, queue);
+    orc_flip_u16(Lx, Ly, q, label, seed, t, cq, NULL);
+    if (obs) {
+      orc_sums sm;
+      orc_sums_u16(Lx, Ly, per_x, per_y, q, &sm);
       orc_derive(&sm, beta, &obs[s]);
     }
   }

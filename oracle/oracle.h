@@ -31,7 +31,9 @@
  *             (the paper's helicity-modulus PCC rule, Sec. 2, after Eq. (6)).
  *
  * All floating point is FP64 except where the stored-angle format fixes FP32
- * (or FP16) arithmetic: the flip and the initial angles.  Built with
+ * (or FP16) arithmetic: the flip and the initial angles.  The u16 variant
+ * (theta = q 2pi / 65536, a storage format that is not the paper's) puts the
+ * axis on the angle grid so that its flip is exact integer arithmetic.  Built with
  * -ffp-contract=off and without -ffast-math.
  */
 #ifndef XY_ORACLE_H
@@ -91,12 +93,20 @@ void orc_philox_stream(uint64_t seed, const uint32_t ctr[4], int word,
 /* ---- one sweep, step by step -------------------------------------------- */
 /* Step 1: axis of sweep t.  out: phi, cos phi, sin phi, C (FP64); c32: C32. */
 void orc_axis(uint64_t seed, uint32_t t, double out[4], float *c32);
+/* u16 fixed-point angles (theta = q 2pi / 65536; a storage variant, not the
+ * paper's): the axis on the reflection grid.  out: phi_q = pi m / 65536,
+ * cos, sin (FP64), C = Cq 2pi / 65536; cq = (m + 32768) mod 65536, with m the
+ * 16 axis-word bits below the top one (phi mod pi floored to the grid). */
+void orc_axis_u16(uint64_t seed, uint32_t t, double out[4], uint16_t *cq);
 
 /* Initial angles: start 0 = random (domain INIT), 1 = ordered (theta = 0). */
 void orc_init_angles_f32(int Lx, int Ly, uint64_t seed, int start,
                          float *theta);
 void orc_init_angles_f16(int Lx, int Ly, uint64_t seed, int start,
                          uint16_t *theta_bits);
+/* u16: q = the top 16 bits of the INIT word the FP32 start uses. */
+void orc_init_angles_u16(int Lx, int Ly, uint64_t seed, int start,
+                         uint16_t *q);
 
 /* Step 2: bonds.  right[i], down[i] in {0,1}.  Returns the number of bonds
  * whose |u - p| < 1e-12 (the reported exception band of exact mode). */
@@ -106,9 +116,16 @@ long orc_bonds_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
 long orc_bonds_f16(int Lx, int Ly, int per_x, int per_y,
                    const uint16_t *theta_bits, double beta, uint64_t seed,
                    uint32_t t, uint8_t *right, uint8_t *down);
+/* u16: angles q 2pi / 65536 in FP64, axis of orc_axis_u16. */
+long orc_bonds_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
+                   double beta, uint64_t seed, uint32_t t, uint8_t *right,
+                   uint8_t *down);
 /* Bond probability bookkeeping for a single bond (for the band report):
  * writes u and p of the right (dir 0) or down (dir 1) bond of site i. */
 void orc_bond_up_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
+                     double beta, uint64_t seed, uint32_t t, int64_t i,
+                     int dir, double *u, double *p);
+void orc_bond_up_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
                      double beta, uint64_t seed, uint32_t t, int64_t i,
                      int dir, double *u, double *p);
 
@@ -125,6 +142,9 @@ long orc_flip_f32(int Lx, int Ly, float *theta, const uint32_t *label,
                   uint64_t seed, uint32_t t, float c32, uint8_t *flipped);
 long orc_flip_f16(int Lx, int Ly, uint16_t *theta_bits, const uint32_t *label,
                   uint64_t seed, uint32_t t, float c32, uint8_t *flipped);
+/* u16: q' = (cq - q) mod 65536 for flipped sites (cq from orc_axis_u16). */
+long orc_flip_u16(int Lx, int Ly, uint16_t *q, const uint32_t *label,
+                  uint64_t seed, uint32_t t, uint16_t cq, uint8_t *flipped);
 /* coin of a root site: 1 = the cluster is reflected. */
 int orc_coin(uint64_t seed, uint32_t t, uint32_t root);
 
@@ -133,6 +153,8 @@ void orc_sums_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,
                   orc_sums *s);
 void orc_sums_f16(int Lx, int Ly, int per_x, int per_y,
                   const uint16_t *theta_bits, orc_sums *s);
+void orc_sums_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
+                  orc_sums *s);
 void orc_derive(const orc_sums *s, double beta, orc_obs *o);
 
 /* Step 6: PCC beta update (the paper's helicity-modulus rule).
@@ -154,6 +176,10 @@ void orc_sw_run_f16(int Lx, int Ly, int per_x, int per_y,
                     uint16_t *theta_bits, double beta, uint64_t seed,
                     uint32_t t0, uint32_t n, uint8_t *right, uint8_t *down,
                     uint32_t *label, uint32_t *queue, orc_obs *obs);
+void orc_sw_run_u16(int Lx, int Ly, int per_x, int per_y, uint16_t *q,
+                    double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                    uint8_t *right, uint8_t *down, uint32_t *label,
+                    uint32_t *queue, orc_obs *obs);
 
 /* PCC run on a periodic L x L lattice: sweeps t0 .. t0+n-1 (Philox sweep
  * counter).  k0 is the number of sweeps already run under PCC; the sweep with

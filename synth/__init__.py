@@ -16,8 +16,11 @@ TWO_PI_F32 = np.float32(2.0 * math.pi)
 
 
 def angles(n: int, seed: int, dtype=np.float32) -> np.ndarray:
-    """n angles uniform in [0, 2pi) stored as dtype (float32 or float16)."""
+    """n angles uniform in [0, 2pi) stored as dtype: float32, float16, or
+    uint16 (fixed point: theta = q 2pi / 65536, q uniform over all 65536)."""
     rng = np.random.default_rng(seed)
+    if dtype == np.uint16:
+        return rng.integers(0, 65536, size=n, dtype=np.uint16)
     a = rng.uniform(0.0, 2.0 * math.pi, size=n).astype(np.float32)
     a[a >= TWO_PI_F32] = 0.0
     if dtype == np.float16:

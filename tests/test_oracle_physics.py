@@ -306,3 +306,127 @@ def test_chik_uniform_and_staggered(orc):
     th = np.zeros(L * L, np.float32)
     th[3 * L + 5] = np.float32(math.pi)
     assert orc.measure(th, L, L, 1.0)["chik"] == pytest.approx((4 + 4) / (2 * L * L), rel=1e-6)
+
+
+# ------------------------------------------------- u16 fixed-point angles
+# theta = q 2pi / 65536.  The axis sits on the reflection grid, so the flip is
+# the integer map q -> (Cq - q) mod 65536 and the update is an exact cluster
+# move of the 65536-state clock model.
+U16_STEP = 2 * math.pi / 65536
+
+
+def test_u16_axis_is_the_fp32_axis_on_the_grid(orc):
+    """phi_q is phi (of the FP32-angle axis, pinned above) reduced mod pi and
+    floored to the grid pi/65536; pi + 2 phi_q = Cq 2pi/65536; m is uniform."""
+    ms = []
+    for t in range(3000):
+        phi = orc.axis(13, t)[0]
+        phq, c, s, C64, cq = orc.axis_u16(13, t)
+        d = math.fmod(phi, math.pi) - phq
+        assert -1e-12 <= d < math.pi / 65536 + 1e-12, (t, phi, phq)
+        assert c == math.cos(phq) and s == math.sin(phq)
+        assert C64 == cq * U16_STEP
+        assert math.cos(math.pi + 2 * phq) == pytest.approx(math.cos(C64), abs=1e-12)
+        assert math.sin(math.pi + 2 * phq) == pytest.approx(math.sin(C64), abs=1e-12)
+        ms.append(int(round(phq / (math.pi / 65536))))
+    h = np.histogram(ms, bins=16, range=(0, 65536))[0]
+    e = len(ms) / 16
+    assert ((h - e) ** 2 / e).sum() < 15 + 5 * math.sqrt(30)
+
+
+def test_u16_flip_is_exact_vector_reflection(orc):
+    """Every flipped q' is the reflection s - 2 (s.r) r of q about the grid
+    axis, to FP64 rounding; the projection on r is exactly negated (this is
+    what makes the move exact); flipping twice restores every bit."""
+    L, seed = 24, 8
+    q0 = synth.angles(L * L, seed=14, dtype=np.uint16)
+    for t in range(6):
+        phq, c, s, C64, cq = orc.axis_u16(seed, t)
+        right, down, _ = orc.bonds(q0, L, L, 1.0, seed, t)
+        lab, _ = orc.label_bfs(right, down, L, L)
+        q = q0.copy()
+        fl = orc.flip(q, lab, L, L, seed, t, cq)
+        old = q0.astype(np.float64) * U16_STEP
+        new = q.astype(np.float64) * U16_STEP
+        proj = np.cos(old) * c + np.sin(old) * s
+        rx, ry = np.cos(old) - 2 * proj * c, np.sin(old) - 2 * proj * s
+        d = np.abs(np.angle(np.exp(1j * (new - np.arctan2(ry, rx)))))
+        assert np.all(d[fl == 1] < 1e-12)
+        newproj = np.cos(new) * c + np.sin(new) * s
+        assert np.all(np.abs(newproj[fl == 1] + proj[fl == 1]) < 1e-12)
+        np.testing.assert_array_equal(q[fl == 0], q0[fl == 0])
+        orc.flip(q, lab, L, L, seed, t, cq)
+        np.testing.assert_array_equal(q, q0)
+
+
+def test_u16_init_is_the_fp32_start_truncated(orc):
+    """q = the top 16 of the 24 bits that the FP32 start scales by 2pi 2^-24."""
+    th = orc.init_angles(64, 3, start=0)
+    q = orc.init_angles(64, 3, start=0, dtype=np.uint16)
+    assert q.dtype == np.uint16
+    step = np.float32(2 * math.pi) * np.float32(2.0 ** -24)
+    # the FP32 start rounds w24 * step to 24 bits, so w24 comes back within 1
+    w24 = np.rint(th.astype(np.float64) / float(step)).astype(np.int64)
+    ok = th > 0  # the FP32 start wraps a value that rounds to 2pi to 0
+    d = (w24[ok] >> 8) - q[ok].astype(np.int64)
+    edge = np.isin(w24[ok] & 255, (0, 255))
+    assert np.all(d[~edge] == 0) and np.all(np.abs(d[edge]) <= 1)
+    assert edge.sum() < 0.02 * ok.sum()
+    assert not orc.init_angles(16, 3, start=1, dtype=np.uint16).any()
+
+
+@pytest.mark.parametrize("L,k", [(16, 1), (32, 3)])
+def test_u16_observables_twisted(orc, L, k):
+    """q = k x 65536 / L is exactly a twist by 2 pi k / L."""
+    y, x = np.mgrid[0:L, 0:L]
+    q = ((k * x * (65536 // L)) % 65536).astype(np.uint16).ravel()
+    o = orc.measure(q, L, L, 0.9)
+    a = 2 * math.pi * k / L
+    assert o["ex"] == pytest.approx(math.cos(a), abs=1e-14)
+    assert o["sx"] == pytest.approx(-math.sin(a), abs=1e-14)
+    assert o["ey"] == pytest.approx(1.0, abs=1e-14)
+    assert o["m2"] == pytest.approx(0.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("beta", [1.0, 3.0])
+def test_u16_open_chain_closed_form(orc, beta):
+    """The 65536-state clock chain is the XY chain to ~1e-9: I1/I0 per link."""
+    N, n = 64, 20000
+    seed = 300 + int(beta * 10)
+    q = orc.init_angles(N, seed, start=0, Ly=1, dtype=np.uint16)
+    obs = orc.sw_run(q, N, 1, beta, seed, 0, n, per_x=0, per_y=0)
+    t = iv(1, beta) / iv(0, beta)
+    m, e = mean_err((obs["ex"] * N / (N - 1))[200:])
+    assert abs(m - t) < 4 * e + 1e-4, (m, e, t)
+
+
+def test_u16_chain_matches_fp32_chain(orc):
+    """L = 16, beta = 1.0: u16 and FP32 chains sample the same distribution."""
+    L, beta, n = 16, 1.0, 12000
+    a = orc.sw_run(orc.init_angles(L, 41, 0), L, L, beta, 41, 0, n)
+    b = orc.sw_run(orc.init_angles(L, 42, 0, dtype=np.uint16), L, L, beta, 42, 0, n)
+    for f in ("energy_per_site", "m2"):
+        ma, ea = mean_err(a[f][500:])
+        mb, eb = mean_err(b[f][500:])
+        assert abs(ma - mb) < 4 * math.hypot(ea, eb), (f, ma, ea, mb, eb)
+
+
+def test_u16_bonds_use_the_grid_axis(orc):
+    """Bonds project on the grid axis phi_q itself: spins exactly perpendicular
+    to it (q = (m + 32768) / 2) get no bond even at beta = 1e12, spins along it
+    (q = m / 2) all get one.  With the unrounded axis phi the perpendicular
+    spins would project to ~pi/65536 and bond."""
+    L, seed, tested = 8, 31, 0
+    for t in range(40):
+        phq, c, s, C64, cq = orc.axis_u16(seed, t)
+        m = int(round(phq / (math.pi / 65536)))
+        if m % 2:
+            continue
+        tested += 1
+        perp = np.full(L * L, (m + 32768) // 2, np.uint16)
+        r, d, _ = orc.bonds(perp, L, L, 1e12, seed, t)
+        assert not r.any() and not d.any(), t
+        par = np.full(L * L, m // 2, np.uint16)
+        r, d, _ = orc.bonds(par, L, L, 1e12, seed, t)
+        assert r.all() and d.all(), t
+    assert tested >= 10
