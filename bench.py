@@ -238,6 +238,7 @@ def run_ours(args):
         out["e2e"] = e2e
         if args.exact_report:
             out["exact_mode"] = exact_report(xy, L, beta, args)
+            out["storage"] = storage_report(xy, L, beta, args)
         if args.big and ws == 1:
             out["l65536"] = run_big(xy, args)
         if args.batched:
@@ -297,6 +298,34 @@ def exact_report(xy, L, beta, args):
     lat.close()
     return {"value": round(L * L / (ms * 1e6), 3), "unit": UNIT, "ms_per_step": round(ms, 5),
             "fp64_band_fraction": n64 / bonds, "fp32_bond_mismatch_rate": wrong / bonds}
+
+
+def storage_report(xy, L, beta, args):
+    """The same sweep (FP32 thresholds) with FP32, FP16 and u16 angle
+    storage: rate and per-kernel times at the benchmark size."""
+    import torch
+
+    out = {}
+    n = max(20, min(200, args.steps))
+    for dt in ("f32", "f16", "u16"):
+        lat = xy.Lattice(L, beta, seed=4343, tile_y=args.tile_y, exact=bool(args.exact), dtype=dt)
+        lat.sweep(5)
+        torch.cuda.synchronize()
+        lat.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        lat.sweep(n)
+        e1.record(lat.stream)
+        torch.cuda.synchronize()
+        kt = lat.profile_read()
+        lat.profile(False)
+        ms = e0.elapsed_time(e1) / n
+        out[dt] = {"value": round(L * L / (ms * 1e6), 3), "unit": UNIT, "ms_per_step": round(ms, 5),
+                   "bytes_per_angle": {"f32": 4, "f16": 2, "u16": 2}[dt],
+                   "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in kt.items()}}
+        lat.close()
+    return out
 
 
 def run_big(xy, args):
@@ -420,15 +449,16 @@ def run_serving(xy, args):
 
 
 def run_precision(xy, args):
-    """Observable shift of FP32 thresholds and FP16 angle storage against the
-    exact (FP64-threshold) mode on the same seeds, and the FP32 bond mismatch
-    rate measured by exact mode."""
+    """Observable shift of FP32 thresholds and of FP16 and u16 angle storage
+    against the exact (FP64-threshold) mode on the same seeds, and the FP32
+    bond mismatch rate measured by exact mode."""
     import numpy as np
 
     L, beta, n = args.prec_L, 1.12, args.prec_sweeps
     res = {}
     for name, kw in (("exact_f32", dict(exact=True)), ("thr_f32", dict(exact=False)),
-                     ("thr_f32_f16", dict(exact=False, dtype="f16"))):
+                     ("thr_f32_f16", dict(exact=False, dtype="f16")),
+                     ("thr_f32_u16", dict(exact=False, dtype="u16"))):
         lat = xy.Lattice(L, beta, 2024, **kw)
         lat.sweep(200)
         lat.measure()
@@ -445,7 +475,7 @@ def run_precision(xy, args):
             blocks = x[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
             stats[f] = (float(blocks.mean()), float(blocks.std(ddof=1) / np.sqrt(nb)))
         res[name] = {f: {"mean": round(m, 6), "err": round(e, 6)} for f, (m, e) in stats.items()}
-    for name in ("thr_f32", "thr_f32_f16"):
+    for name in ("thr_f32", "thr_f32_f16", "thr_f32_u16"):
         res[name]["shift_vs_exact"] = {
             f: round(res[name][f]["mean"] - res["exact_f32"][f]["mean"], 6)
             for f in ("energy_per_site", "m2", "beta_upsilon")}

@@ -57,7 +57,18 @@ typedef enum {
 
 typedef struct xy_lattice xy_lattice; /* opaque host handle */
 
-typedef enum { XY_F32 = 0, XY_F16 = 1 } xy_angle_t;
+/* Stored angle format.  XY_F32 and XY_F16 hold theta in [0, 2pi) as IEEE
+ * floats; a flipped angle is wrap(C32 - theta) in FP32, rounded to the
+ * format.  XY_U16 is a fixed-point storage variant that the paper does not
+ * have: theta = q 2pi / 65536 with q in 0..65535.  For it, the axis of every
+ * sweep is put on the reflection grid: m = bits 47..62 of the 64-bit axis
+ * word (phi mod pi floored to pi/65536), phi_q = pi m / 65536 and
+ * Cq = (m + 32768) mod 65536.  The flip is then the exact integer map
+ * q -> (Cq - q) mod 65536, and the bonds project on phi_q itself.  Each sweep
+ * is an exact cluster move of the 65536-state clock model, at two bytes per
+ * site and with no rounding in the flip.  The random start takes the top 16
+ * bits of the word that the FP32 start scales. */
+typedef enum { XY_F32 = 0, XY_F16 = 1, XY_U16 = 2 } xy_angle_t;
 
 /* Bond-threshold arithmetic.  XY_THR_F64 ("exact mode") decides every bond as
  * the FP64 rule u < 1 - exp(-2 beta a_i a_j) does: an FP32 evaluation with a
@@ -165,8 +176,9 @@ xy_status xy_get_state(xy_lattice *h, double *beta, uint64_t *sweep);
 xy_status xy_destroy(xy_lattice *h);
 
 /* ---- host copies (synchronising) --------------------------------------- */
-/* Angles: N elements of the lattice dtype (float or IEEE half bits), row-
- * major.  Set values must lie in [0, 2 pi); XY_EINVAL otherwise. */
+/* Angles: N elements of the lattice dtype (float, IEEE half bits or u16 q),
+ * row-major.  Set float/half values must lie in [0, 2 pi); XY_EINVAL
+ * otherwise (every u16 value is valid). */
 xy_status xy_get_angles(xy_lattice *h, void *host_dst);
 xy_status xy_set_angles(xy_lattice *h, const void *host_src);
 /* Bonds of the last sweep as N bytes each (1 = active): right[i] is the bond

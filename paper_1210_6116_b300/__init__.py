@@ -22,7 +22,15 @@ _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libxy.so"
 
 XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_EINTERNAL, XY_EUNSUPPORTED = range(7)
-XY_F32, XY_F16 = 0, 1
+XY_F32, XY_F16, XY_U16 = 0, 1, 2
+# angle storage by name: (xy_angle_t, numpy dtype of xy_get/set_angles)
+DTYPES = {"f32": (XY_F32, np.float32), "f16": (XY_F16, np.float16), "u16": (XY_U16, np.uint16)}
+
+
+def _dtype(name: str):
+    if name not in DTYPES:
+        raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
+    return DTYPES[name]
 XY_THR_F32, XY_THR_F64 = 0, 1
 
 STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "XY_ETIMEOUT",
@@ -215,9 +223,9 @@ class Lattice:
 
         self.L = int(L)
         self.dtype = dtype
-        self.np_dtype = np.float32 if dtype == "f32" else np.float16
+        code, self.np_dtype = _dtype(dtype)
         self.cfg = xy_config(L=self.L, tile_y=tile_y, seed=seed, beta=beta,
-                             angle_dtype=XY_F32 if dtype == "f32" else XY_F16,
+                             angle_dtype=code,
                              threshold_mode=XY_THR_F64 if exact else XY_THR_F32,
                              start=0 if start == "random" else 1, record_cap=record_cap,
                              measure_xi=1 if measure_xi else 0)
@@ -329,7 +337,7 @@ class Engine:
         import torch
 
         self.dtype = dtype
-        self.np_dtype = np.float32 if dtype == "f32" else np.float16
+        code, self.np_dtype = _dtype(dtype)
         self.exact = exact
         self.tile_y = tile_y
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -338,7 +346,7 @@ class Engine:
         self.table = torch.empty(n.value, dtype=torch.uint8, device="cuda")
         self.handle = ctypes.c_void_p()
         _check(load_library().xy_engine_create(
-            max_slots, XY_F32 if dtype == "f32" else XY_F16,
+            max_slots, code,
             XY_THR_F64 if exact else XY_THR_F32, tile_y,
             ctypes.c_void_p(self.table.data_ptr()), n.value,
             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.handle)))
@@ -348,7 +356,7 @@ class Engine:
     def config(self, L: int, beta: float, seed: int, start: str = "random",
                record_cap: int = 0, measure_xi: bool = False) -> xy_config:
         return xy_config(L=L, tile_y=self.tile_y, seed=seed, beta=beta,
-                         angle_dtype=XY_F32 if self.dtype == "f32" else XY_F16,
+                         angle_dtype=_dtype(self.dtype)[0],
                          threshold_mode=XY_THR_F64 if self.exact else XY_THR_F32,
                          start=0 if start == "random" else 1, record_cap=record_cap,
                          measure_xi=1 if measure_xi else 0)

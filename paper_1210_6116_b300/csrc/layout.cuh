@@ -41,8 +41,8 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
     return layout_fail(XY_EINVAL, "L outside 2..65536");
   if (!(c->beta >= 0.0) || !std::isfinite(c->beta))
     return layout_fail(XY_EINVAL, "beta must be finite and >= 0");
-  if (c->angle_dtype != XY_F32 && c->angle_dtype != XY_F16)
-    return layout_fail(XY_EINVAL, "angle_dtype must be XY_F32 or XY_F16");
+  if (c->angle_dtype != XY_F32 && c->angle_dtype != XY_F16 && c->angle_dtype != XY_U16)
+    return layout_fail(XY_EINVAL, "angle_dtype must be XY_F32, XY_F16 or XY_U16");
   if (c->threshold_mode != XY_THR_F32 && c->threshold_mode != XY_THR_F64)
     return layout_fail(XY_EINVAL, "threshold_mode must be XY_THR_F32 or XY_THR_F64");
   if (c->start != 0 && c->start != 1)

@@ -32,6 +32,8 @@
 #include <cuda_fp16.h>
 #include <cstdint>
 
+#include <type_traits>
+
 #include "philox.cuh"
 
 namespace xyk {
@@ -68,7 +70,8 @@ struct DevState {
   float eps;             // half-width of the FP32 error band of exact mode
   uint32_t pcc_on;
   // helicity-modulus PCC
-  uint32_t pcc_block, pcc_halve, pcc_count, pad1;
+  uint32_t pcc_block, pcc_halve, pcc_count;
+  uint32_t quant;  // 1: u16 angles, axis on the reflection grid
   double pcc_target, pcc_dbeta0, pcc_acc;
   uint64_t pcc_k;
   // records
@@ -110,6 +113,13 @@ __device__ __forceinline__ float load_angle<__half>(const __half *p,
                                                     uint64_t i) {
   return __half2float(__ldg(p + i));
 }
+// u16 fixed point: the stored q itself (exact in FP32); the angle is
+// q 2pi / 65536, see angle_f32 / angle_f64 below
+template <>
+__device__ __forceinline__ float load_angle<uint16_t>(const uint16_t *p,
+                                                      uint64_t i) {
+  return static_cast<float>(__ldg(p + i));
+}
 
 // wrap an FP32 angle in (-2pi, 2pi] into [0, 2pi) with FP32 adds
 __device__ __forceinline__ float wrap_angle(float v) {
@@ -131,15 +141,55 @@ __device__ __forceinline__ __half store_value<__half>(float v) {
   if (back >= two_pi_f()) h = __float2half_rn(__fadd_rn(back, -two_pi_f()));
   return h;
 }
-template <typename AT>
-__device__ __forceinline__ float stored_float(AT v);
 template <>
-__device__ __forceinline__ float stored_float<float>(float v) {
-  return v;
+__device__ __forceinline__ uint16_t store_value<uint16_t>(float v) {
+  return static_cast<uint16_t>(static_cast<uint32_t>(v));  // v is an exact q
+}
+
+// Kernels hold every stored angle as a float that equals the stored value
+// exactly ("raw": the FP32 angle, the FP16 angle widened, or u16's q).  The
+// traits below turn a raw value into radians and apply the reflection.
+template <typename AT>
+__device__ __forceinline__ float angle_f32(float raw) {  // radians, FP32
+  return raw;
 }
 template <>
-__device__ __forceinline__ float stored_float<__half>(__half v) {
-  return __half2float(v);
+__device__ __forceinline__ float angle_f32<uint16_t>(float raw) {
+  return __fmul_rn(raw, 6.2831854820251465f * 0x1p-16f);  // q 2pi_f 2^-16
+}
+template <typename AT>
+__device__ __forceinline__ double angle_f64(float raw) {  // radians, FP64
+  return static_cast<double>(raw);
+}
+template <>
+__device__ __forceinline__ double angle_f64<uint16_t>(float raw) {
+  return __dmul_rn(static_cast<double>(raw), 6.283185307179586 * 0x1p-16);
+}
+// reflected raw value: wrap(c - theta) in FP32, rounded to the storage format;
+// u16: (Cq - q) mod 65536 in integers (c holds Cq)
+template <typename AT>
+__device__ __forceinline__ float reflect(float raw, float c);
+template <>
+__device__ __forceinline__ float reflect<float>(float raw, float c) {
+  return wrap_angle(__fadd_rn(c, -raw));
+}
+template <>
+__device__ __forceinline__ float reflect<__half>(float raw, float c) {
+  return __half2float(store_value<__half>(wrap_angle(__fadd_rn(c, -raw))));
+}
+template <>
+__device__ __forceinline__ float reflect<uint16_t>(float raw, float c) {
+  const uint32_t q = static_cast<uint32_t>(raw), cq = static_cast<uint32_t>(c);
+  return static_cast<float>((cq + 65536u - q) & 0xFFFFu);
+}
+// sin and cos of the angle for the observables (accurate, not the SFU)
+template <typename AT>
+__device__ __forceinline__ void sin_cos(float raw, float *s, float *c) {
+  sincosf(raw, s, c);
+}
+template <>
+__device__ __forceinline__ void sin_cos<uint16_t>(float raw, float *s, float *c) {
+  sincospif(raw * 0x1p-15f, s, c);  // q 2^-15 is exact: sin(pi q / 32768)
 }
 
 // projection s.r in FP32 from the stored angle; sin/cos through the SFU on
@@ -151,10 +201,10 @@ __device__ __forceinline__ float project32(float th, float cphi, float sphi) {
 }
 
 // FP64 projection exactly as the rule defines it: cos(th) cphi + sin(th) sphi
-__device__ __forceinline__ double project64(float th, double cphi,
+__device__ __forceinline__ double project64(double th, double cphi,
                                             double sphi) {
   double s, c;
-  sincos(static_cast<double>(th), &s, &c);
+  sincos(th, &s, &c);
   return __dadd_rn(__dmul_rn(c, cphi), __dmul_rn(s, sphi));
 }
 
@@ -192,8 +242,8 @@ __device__ __forceinline__ Tile tile_geom(uint32_t L, uint32_t ntx,
 // ---------------------------------------------------------------------------
 // FP64 rule, operation for operation: x = a_i a_j; active iff x > 0 and
 // (w + 1/2) 2^-32 < 1 - exp(-2 beta x).
-static __device__ __noinline__ bool bond_fp64(float th_i, float th_j, uint32_t word,
-                                       double beta, double cphi, double sphi) {
+static __device__ __noinline__ bool bond_fp64(double th_i, double th_j, uint32_t word,
+                                              double beta, double cphi, double sphi) {
   const double ai = project64(th_i, cphi, sphi);
   const double aj = project64(th_j, cphi, sphi);
   const double x = __dmul_rn(ai, aj);
@@ -419,8 +469,8 @@ __global__ void __launch_bounds__(kThreads, 4)
         tc = load_angle(th, static_cast<uint64_t>(g.y0 + r0 + lane) * L + g.xh);
       float a[B + 1];
 #pragma unroll
-      for (int k = 0; k <= B; ++k) a[k] = project32(tv[k], cphi, sphi);
-      const float ac = project32(tc, cphi, sphi);
+      for (int k = 0; k <= B; ++k) a[k] = project32(angle_f32<AT>(tv[k]), cphi, sphi);
+      const float ac = project32(angle_f32<AT>(tc), cphi, sphi);
 
       // phase A: bonds and coins of every row of the band (rows are
       // independent here, so their Philox chains overlap)
@@ -457,13 +507,15 @@ __global__ void __launch_bounds__(kThreads, 4)
                 const float th_r = (static_cast<uint32_t>(lane) + 1u == g.w)
                                        ? load_angle(th, static_cast<uint64_t>(gy) * L + g.xh)
                                        : load_angle(th, static_cast<uint64_t>(i) + 1u);
-                const bool e = bond_fp64(tv[k], th_r, rn.w0, st->beta, st->cphi, st->sphi);
+                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(th_r), rn.w0,
+                                         st->beta, st->cphi, st->sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != br) atomicAdd(&st->n_fp32_wrong, 1ull);
                 br = e;
               }
               if (amb_d) {
-                const bool e = bond_fp64(tv[k], tv[k + 1], rn.w1, st->beta, st->cphi, st->sphi);
+                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(tv[k + 1]), rn.w1,
+                                         st->beta, st->cphi, st->sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != bd) atomicAdd(&st->n_fp32_wrong, 1ull);
                 bd = e;
@@ -773,21 +825,16 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
     for (int k = 0; k <= B; ++k) {
       float nv = t[k];
       if (f[k]) {
-        const AT sv = store_value<AT>(wrap_angle(__fadd_rn(c32, -t[k])));
-        nv = stored_float<AT>(sv);
+        nv = reflect<AT>(t[k], c32);
         if (static_cast<uint32_t>(k) < nb && col_ok)
-          thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = sv;
+          thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_value<AT>(nv);
       } else if (static_cast<uint32_t>(k) < nb && col_ok) {
         thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_value<AT>(t[k]);
       }
-      sincosf(nv, &sn[k], &co[k]);
+      sin_cos<AT>(nv, &sn[k], &co[k]);
     }
     float cc, sc;
-    {
-      float nv = tc;
-      if (fc) nv = stored_float<AT>(store_value<AT>(wrap_angle(__fadd_rn(c32, -tc))));
-      sincosf(nv, &sc, &cc);
-    }
+    sin_cos<AT>(fc ? reflect<AT>(tc, c32) : tc, &sc, &cc);
     // observable terms of the band's own sites (with d.xi also the Fourier
     // sums of chik: s(r) times (cos, sin)(2 pi x / L) and (2 pi y / L))
     constexpr int NV = XI ? 14 : 6;
@@ -868,14 +915,24 @@ __device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta,
                                         uint32_t k0, uint32_t k1) {
   const Words4 w = philox4x32_10(0u, 0u, t, kDomAxis, k0, k1);
   const uint64_t bits = (static_cast<uint64_t>(w.w0) << 32) | w.w1;
-  const double u = static_cast<double>(bits >> 11) * 0x1p-53;
-  const double phi = __dmul_rn(6.283185307179586, u);
   double s, c;
-  sincos(phi, &s, &c);
-  const double C = fmod(__dadd_rn(3.141592653589793, __dmul_rn(2.0, phi)),
-                        6.283185307179586);
-  float c32 = __double2float_rn(C);
-  if (c32 >= two_pi_f()) c32 = 0.0f;
+  float c32;
+  if (st->quant) {
+    // u16 angles: the axis on the reflection grid, phi_q = pi m / 65536 with
+    // m = phi mod pi floored to the grid, and Cq = m + 32768 (mod 65536), so
+    // that pi + 2 phi_q = Cq 2pi / 65536 and the flip is q -> Cq - q
+    const uint32_t m = static_cast<uint32_t>(bits >> 47) & 0xFFFFu;
+    sincospi(static_cast<double>(m) * 0x1p-16, &s, &c);
+    c32 = static_cast<float>((m + 32768u) & 0xFFFFu);
+  } else {
+    const double u = static_cast<double>(bits >> 11) * 0x1p-53;
+    const double phi = __dmul_rn(6.283185307179586, u);
+    sincos(phi, &s, &c);
+    const double C = fmod(__dadd_rn(3.141592653589793, __dmul_rn(2.0, phi)),
+                          6.283185307179586);
+    c32 = __double2float_rn(C);
+    if (c32 >= two_pi_f()) c32 = 0.0f;
+  }
   st->t = t;
   st->beta = beta;
   st->cphi = c;
@@ -884,8 +941,10 @@ __device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta,
   st->sphi32 = __double2float_rn(s);
   st->c32 = c32;
   st->beta2_32 = __double2float_rn(2.0 * beta);
-  // band half-width: 4x the error bound of the FP32 evaluation of u - p
-  st->eps = __double2float_rn(4.0 * (2.0 * beta * 2.0e-6 + 3.0e-7) + 0x1p-24);
+  // band half-width: 4x the error bound of the FP32 evaluation of u - p;
+  // u16 adds <= 4.2e-7 per projection for the FP32 angle q 2pi_f 2^-16
+  const double dx = st->quant ? 3.0e-6 : 2.0e-6;
+  st->eps = __double2float_rn(4.0 * (2.0 * beta * dx + 3.0e-7) + 0x1p-24);
 }
 
 // K5: one warp per lattice
@@ -967,9 +1026,13 @@ __global__ void k_init_angles(LatDesc d, int ordered) {
       const Words4 w = philox4x32_10(static_cast<uint32_t>(i),
                                      static_cast<uint32_t>(i >> 32),
                                      0xFFFFFFFFu, kDomInit, d.key0, d.key1);
-      const float step = 6.2831854820251465f * 0x1p-24f;
-      v = __fmul_rn(static_cast<float>(w.w0 >> 8), step);
-      if (v >= two_pi_f()) v = 0.0f;
+      if constexpr (std::is_same<AT, uint16_t>::value) {
+        v = static_cast<float>(w.w0 >> 16);  // q: the word's top 16 bits
+      } else {
+        const float step = 6.2831854820251465f * 0x1p-24f;
+        v = __fmul_rn(static_cast<float>(w.w0 >> 8), step);
+        if (v >= two_pi_f()) v = 0.0f;
+      }
     }
     th[i] = store_value<AT>(v);
   }
@@ -984,8 +1047,9 @@ static __global__ void k_init_wave(LatDesc d) {
   const_cast<float2 *>(d.wave)[x] = make_float2(__double2float_rn(c), __double2float_rn(s));
 }
 
-static __global__ void k_init_state(LatDesc d, double beta) {
+static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   DevState *st = d.st;
+  st->quant = quant;
   st->cur = 0;
   st->pcc_on = 0;
   st->pcc_block = 1;

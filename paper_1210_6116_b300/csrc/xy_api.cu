@@ -147,15 +147,17 @@ cudaError_t dispatch_ty(xy_lattice *h, bool attrs) {
   }
 }
 
-cudaError_t launch_sweep(xy_lattice *h) {
-  return h->cfg.angle_dtype == XY_F32 ? dispatch_ty<float>(h, false)
-                                      : dispatch_ty<__half>(h, false);
+cudaError_t dispatch_dtype(xy_lattice *h, bool attrs) {
+  switch (h->cfg.angle_dtype) {
+    case XY_F32: return dispatch_ty<float>(h, attrs);
+    case XY_F16: return dispatch_ty<__half>(h, attrs);
+    default: return dispatch_ty<uint16_t>(h, attrs);
+  }
 }
 
-cudaError_t set_attrs(xy_lattice *h) {
-  return h->cfg.angle_dtype == XY_F32 ? dispatch_ty<float>(h, true)
-                                      : dispatch_ty<__half>(h, true);
-}
+cudaError_t launch_sweep(xy_lattice *h) { return dispatch_dtype(h, false); }
+
+cudaError_t set_attrs(xy_lattice *h) { return dispatch_dtype(h, true); }
 
 // labeling only, from the bond planes already in the workspace
 template <int TY>
@@ -176,7 +178,7 @@ cudaError_t launch_label_only_t(xy_lattice *h) {
 cudaError_t launch_label_only(xy_lattice *h) {
   if (h->cfg.angle_dtype != XY_F32) {
     // the label-only kernels are dtype-agnostic; make sure their attributes
-    // are set even when the lattice itself is FP16
+    // are set even when the lattice itself stores FP16 or u16 angles
     cudaError_t e;
     switch (h->lo.TY) {
       case 16: e = set_attrs_t<16, float, true>(); break;
@@ -266,15 +268,17 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
   if ((e = cudaMemsetAsync(d.coin, 0, (static_cast<size_t>(lo.L) * lo.L / 32 + 2) * 4,
                            h->stream)) != cudaSuccess)
     return bail("coin reset", e);
-  k_init_state<<<1, 1, 0, h->stream>>>(d, cfg->beta);
+  k_init_state<<<1, 1, 0, h->stream>>>(d, cfg->beta, cfg->angle_dtype == XY_U16 ? 1u : 0u);
   k_init_wave<<<(lo.L + 255) / 256, 256, 0, h->stream>>>(d);
   const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;
   const uint32_t blocks = static_cast<uint32_t>(
       std::min<uint64_t>((n + 255) / 256, static_cast<uint64_t>(h->sm_count) * 16));
   if (cfg->angle_dtype == XY_F32)
     k_init_angles<float><<<blocks, 256, 0, h->stream>>>(d, cfg->start);
-  else
+  else if (cfg->angle_dtype == XY_F16)
     k_init_angles<__half><<<blocks, 256, 0, h->stream>>>(d, cfg->start);
+  else
+    k_init_angles<uint16_t><<<blocks, 256, 0, h->stream>>>(d, cfg->start);
   if ((e = cudaGetLastError()) != cudaSuccess) return bail("init launch", e);
   // the host copies above read stack memory: finish them before returning
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail("init sync", e);
@@ -425,7 +429,7 @@ xy_status xy_set_angles(xy_lattice *h, const void *host_src) {
       if (!(a[i] >= 0.0f && a[i] < two_pi))
         return fail(XY_EINVAL, "angle %llu = %g outside [0, 2pi)",
                     static_cast<unsigned long long>(i), a[i]);
-  } else {
+  } else if (h->cfg.angle_dtype == XY_F16) {
     const __half_raw *a = static_cast<const __half_raw *>(host_src);
     for (uint64_t i = 0; i < n; ++i) {
       const float v = __half2float(__half(a[i]));
@@ -433,7 +437,7 @@ xy_status xy_set_angles(xy_lattice *h, const void *host_src) {
         return fail(XY_EINVAL, "angle %llu = %g outside [0, 2pi)",
                     static_cast<unsigned long long>(i), v);
     }
-  }
+  }  // u16: every q in 0..65535 is an angle in [0, 2pi)
   XY_CUDA(cudaStreamSynchronize(h->stream));
   DevState s;
   XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));

@@ -110,12 +110,16 @@ size_t table_bytes(uint32_t max_slots) {
 void launch_table(xy_engine *e, cudaStream_t s) {
   bool xi = false;
   for (const LatDesc &d : e->h_descs) xi = xi || d.xi;
+  const bool ex = e->thr == XY_THR_F64;
   if (e->dtype == XY_F32) {
-    if (e->thr == XY_THR_F64) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    if (ex) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
     else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
-  } else {
-    if (e->thr == XY_THR_F64) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+  } else if (e->dtype == XY_F16) {
+    if (ex) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
     else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+  } else {
+    if (ex) launch_ty<uint16_t, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    else launch_ty<uint16_t, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
   }
 }
 
@@ -176,7 +180,8 @@ xy_status xy_engine_create(uint32_t max_slots, int angle_dtype, int threshold_mo
   if (!out) return fail(XY_EINVAL, "out is NULL");
   *out = nullptr;
   if (max_slots == 0) return fail(XY_EINVAL, "max_slots must be >= 1");
-  if (angle_dtype != XY_F32 && angle_dtype != XY_F16) return fail(XY_EINVAL, "bad angle_dtype");
+  if (angle_dtype != XY_F32 && angle_dtype != XY_F16 && angle_dtype != XY_U16)
+    return fail(XY_EINVAL, "bad angle_dtype");
   if (threshold_mode != XY_THR_F32 && threshold_mode != XY_THR_F64)
     return fail(XY_EINVAL, "bad threshold_mode");
   if (!tile_ok(tile_y)) return fail(XY_EINVAL, "tile_y must be 16, 32, 64 or 128");
@@ -229,14 +234,16 @@ xy_status xy_engine_admit(xy_engine *e, const xy_config *cfg, const xy_pcc_param
   s.desc = make_desc(&c, lo, static_cast<char *>(d_workspace));
   XY_CUDA(cudaMemsetAsync(s.desc.acc, 0, sizeof(long long) * kSlots * kAccStride, e->stream));
   XY_CUDA(cudaMemsetAsync(s.desc.coin, 0, (static_cast<size_t>(lo.L) * lo.L / 32 + 2) * 4, e->stream));
-  k_init_state<<<1, 1, 0, e->stream>>>(s.desc, c.beta);
+  k_init_state<<<1, 1, 0, e->stream>>>(s.desc, c.beta, c.angle_dtype == XY_U16 ? 1u : 0u);
   k_init_wave<<<(lo.L + 255) / 256, 256, 0, e->stream>>>(s.desc);
   const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;
   const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((n + 255) / 256, 4096));
   if (c.angle_dtype == XY_F32)
     k_init_angles<float><<<blocks, 256, 0, e->stream>>>(s.desc, c.start);
-  else
+  else if (c.angle_dtype == XY_F16)
     k_init_angles<__half><<<blocks, 256, 0, e->stream>>>(s.desc, c.start);
+  else
+    k_init_angles<uint16_t><<<blocks, 256, 0, e->stream>>>(s.desc, c.start);
   if (pcc)
     k_set_pcc<<<1, 1, 0, e->stream>>>(s.desc.st, 1u, pcc->target, pcc->dbeta0, pcc->halve_every,
                                       pcc->block);

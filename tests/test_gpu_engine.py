@@ -33,7 +33,8 @@ def _alone(L, beta, seed, n, *, dtype="f32", exact=False, tile_y=32, pcc=None, s
     return lat.measure(), lat.get_angles()
 
 
-@pytest.mark.parametrize("dtype,exact", [("f32", False), ("f32", True), ("f16", False)])
+@pytest.mark.parametrize("dtype,exact", [("f32", False), ("f32", True), ("f16", False),
+                                         ("u16", False), ("u16", True)])
 def test_mixed_batch_equals_alone(dtype, exact):
     table = synth.replica_table(12, seed=5, sizes=(64, 128, 256, 512), beta_range=(1.0, 1.3))
     eng = xy.Engine(len(table), dtype=dtype, exact=exact, tile_y=32)

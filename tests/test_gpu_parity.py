@@ -39,6 +39,8 @@ def test_random_start_bit_exact(orc, L):
                                   orc.init_angles(L, 12345, 0, dtype=np.float16).view(np.uint16))
     lat0 = _lat(L, 1.0, 7, start="ordered")
     assert not lat0.get_angles().any()
+    lat_q = _lat(L, 1.0, 12345, start="random", dtype="u16")
+    np.testing.assert_array_equal(lat_q.get_angles(), orc.init_angles(L, 12345, 0, dtype=np.uint16))
 
 
 # ---------------------------------------------------- one sweep, step by step
@@ -74,6 +76,71 @@ def test_single_sweep_steps(orc, L, ty, beta):
     o = orc.measure(th, L, L, beta)
     bad = obs_close(rec_dict(rec[0]), o, L * L, beta)
     assert not bad, bad
+
+
+# ------------------------------------------------- u16 fixed-point angles
+@pytest.mark.parametrize("L,ty", [(3, 16), (33, 16), (64, 32), (130, 64), (257, 128)])
+@pytest.mark.parametrize("beta", [0.0, 1.12, 3.0])
+def test_u16_single_sweep_steps(orc, L, ty, beta):
+    """u16 angles: bonds on the grid axis (exact mode), labels, the integer
+    flip bit for bit, observables within tolerance."""
+    seed = 2000 + L
+    q0 = synth.angles(L * L, seed=L * 5 + 3, dtype=np.uint16)
+    lat = _lat(L, beta, seed, tile_y=ty, dtype="u16")
+    lat.set_angles(q0)
+    lat.sweep(1)
+    rec = lat.measure()
+    g_r, g_d = lat.get_bonds()
+    o_r, o_d, _ = orc.bonds(q0, L, L, beta, seed, 0)
+    inside, outside = band_mismatches(orc, q0, L, beta, seed, 0, g_r, g_d, o_r, o_d)
+    assert not outside, outside[:5]
+    assert len(inside) == 0
+    g_lab = lat.get_labels()
+    np.testing.assert_array_equal(g_lab, orc.label_bfs(g_r, g_d, L, L)[0])
+    q = q0.copy()
+    orc.flip(q, g_lab, L, L, seed, 0, orc.axis_u16(seed, 0)[4])
+    np.testing.assert_array_equal(lat.get_angles(), q)
+    bad = obs_close(rec_dict(rec[0]), orc.measure(q, L, L, beta), L * L, beta)
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("exact,geoms,n", [(True, ((64, 32), (96, 64)), 300),
+                                           (False, ((64, 32),), 30)])
+def test_u16_chain_bit_exact(orc, exact, geoms, n):
+    """Chains from the random start: angles bit-exact and every record within
+    tolerance.  Exact mode: 300 sweeps at L = 64 and L = 96 (ragged tile
+    rows).  FP32 thresholds: 30 sweeps at L = 64, where the expected number
+    of bonds that FP32 decides differently from FP64 (~8e-8 per bond) is
+    0.02."""
+    for L, ty in geoms:
+        beta, seed = 1.12, 31 + L
+        lat = _lat(L, beta, seed, tile_y=ty, dtype="u16", exact=exact)
+        q = orc.init_angles(L, seed, 0, dtype=np.uint16)
+        lat.sweep(n)
+        recs = lat.measure()
+        o = orc.sw_run(q, L, L, beta, seed, 0, n)
+        np.testing.assert_array_equal(lat.get_angles(), q)
+        for k in range(n):
+            od = {n: float(o[k][n]) for n in o.dtype.names}
+            assert not obs_close(rec_dict(recs[k]), od, L * L, beta), (L, k)
+
+
+def test_u16_bench_size_one_sweep(orc):
+    """L = 4096, tile 64, one u16 sweep from the random start."""
+    L, beta, seed = 4096, 1.12, 1003
+    lat = _lat(L, beta, seed, tile_y=64, dtype="u16", measure_xi=True)
+    q0 = orc.init_angles(L, seed, 0, dtype=np.uint16)
+    lat.sweep(1)
+    rec = lat.measure()
+    g_r, g_d = lat.get_bonds()
+    o_r, o_d, band = orc.bonds(q0, L, L, beta, seed, 0)
+    assert int((g_r != o_r).sum() + (g_d != o_d).sum()) <= band
+    g_lab = lat.get_labels()
+    np.testing.assert_array_equal(g_lab, orc.label_bfs(g_r, g_d, L, L)[0])
+    q = q0.copy()
+    orc.flip(q, g_lab, L, L, seed, 0, orc.axis_u16(seed, 0)[4])
+    np.testing.assert_array_equal(lat.get_angles(), q)
+    assert not obs_close(rec_dict(rec[0]), orc.measure(q, L, L, beta), L * L, beta, xi=True)
 
 
 # ------------------------------------------------------------ whole chains
