@@ -53,10 +53,11 @@ OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy",
 
 
 class Obs(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in OBS_FIELDS]
+    _fields_ = [(n, ctypes.c_double) for n in OBS_FIELDS + ("flipped",)]
 
 
-OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS])
+# per-update records: the observables and the number of reflected sites
+OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS + ("flipped",)])
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -100,6 +101,12 @@ def lib():
             "orc_sw_run_f16": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, _U32, _P, _P, _P, _P, _P]),
             "orc_pcc_run_f32": (None, [_I, _P, _P, _D, _D, _U32, _U32, _U64, _U32, _U32, _U32,
                                        _P, _P, _P, _P, _P, _P, _P]),
+            "orc_seed_site": (_U64, [_U64, _U32, _U64]),
+            "orc_wolff_cluster": (ctypes.c_long, [_I, _I, _I, _I, _P, _D, _D, _D, _U64, _U32,
+                                                  _U64, _P, _P]),
+            "orc_wolff_run_f32": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, _U32, _P, _P, _P]),
+            "orc_wolff_run_f16": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, _U32, _P, _P, _P]),
+            "orc_wolff_run_u16": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, _U32, _P, _P, _P]),
             "orc_metropolis_run": (None, [_I, _I, _P, _D, _D, _U64, _U32, _U32, _P, _P]),
         }
         for name, (res, args) in sig.items():
@@ -312,3 +319,47 @@ def metropolis_run(theta64: np.ndarray, L: int, beta: float, delta: float, seed:
     lib().orc_metropolis_run(L, L, _ptr(theta64), beta, delta, seed, t0, n, _ptr(obs),
                              ctypes.byref(acc))
     return obs, acc.value
+
+
+# ---- Wolff single-cluster updates -----------------------------------------
+def seed_site(seed: int, t: int, n: int) -> int:
+    return int(lib().orc_seed_site(seed, t, n))
+
+
+def _widen(theta: np.ndarray) -> np.ndarray:
+    if theta.dtype == np.uint16:
+        return theta.astype(np.float64) * (6.283185307179586 / 65536.0)
+    return theta.astype(np.float64)
+
+
+def wolff_cluster(theta: np.ndarray, Lx: int, Ly: int, beta: float, seed: int, t: int,
+                  per_x: int = 1, per_y: int = 1):
+    """(in_cluster bytes, size) of update t's cluster, grown from its seed
+    site on the angles theta (not modified)."""
+    n = Lx * Ly
+    ax = axis_u16(seed, t) if theta.dtype == np.uint16 else axis(seed, t)
+    ang = np.ascontiguousarray(_widen(theta))
+    inc = np.zeros(n, np.uint8)
+    q = np.zeros(n, np.uint32)
+    size = lib().orc_wolff_cluster(Lx, Ly, per_x, per_y, _ptr(ang), ax[1], ax[2], beta, seed, t,
+                                   seed_site(seed, t, n), _ptr(inc), _ptr(q))
+    return inc, int(size)
+
+
+def wolff_run(theta: np.ndarray, Lx: int, Ly: int, beta: float, seed: int, t0: int, n: int,
+              per_x: int = 1, per_y: int = 1, record: bool = True) -> np.ndarray:
+    """n Wolff updates t0..t0+n-1 in place; returns the per-update records
+    (flipped = cluster size)."""
+    N = Lx * Ly
+    inc = np.zeros(N, np.uint8)
+    q = np.zeros(N, np.uint32)
+    obs = np.zeros(n, OBS_DTYPE) if record else None
+    optr = _ptr(obs) if record else None
+    if theta.dtype == np.float32:
+        f, th = lib().orc_wolff_run_f32, theta
+    elif theta.dtype == np.uint16:
+        f, th = lib().orc_wolff_run_u16, theta
+    else:
+        f, th = lib().orc_wolff_run_f16, theta.view(np.uint16)
+    f(Lx, Ly, per_x, per_y, _ptr(th), beta, seed, t0, n, _ptr(inc), _ptr(q), optr)
+    return obs

@@ -605,6 +605,7 @@ void orc_derive(const orc_sums *s, double beta, orc_obs *o) {
     ay += s->fy[k] * s->fy[k];
   }
   o->chik = (ax + ay) / (2.0 * n);
+  o->flipped = 0.0; /* set by the update that produced the configuration */
 }
 
 /* ------------------------------------------------------------------------ */
@@ -636,11 +637,12 @@ void orc_sw_run_f32(int Lx, int Ly, int per_x, int per_y, float *theta,
     orc_axis(seed, t, ax, &c32);
     orc_bonds_f32(Lx, Ly, per_x, per_y, theta, beta, seed, t, right, down);
     orc_label_bfs(Lx, Ly, per_x, per_y, right, down, label, queue);
-    orc_flip_f32(Lx, Ly, theta, label, seed, t, c32, NULL);
+    long flipped = orc_flip_f32(Lx, Ly, theta, label, seed, t, c32, NULL);
     if (obs) {
       orc_sums sm;
       orc_sums_f32(Lx, Ly, per_x, per_y, theta, &sm);
       orc_derive(&sm, beta, &obs[s]);
+      obs[s].flipped = (double)flipped;
     }
   }
 }
@@ -657,11 +659,12 @@ void orc_sw_run_f16(int Lx, int Ly, int per_x, int per_y,
     orc_bonds_f16(Lx, Ly, per_x, per_y, theta_bits, beta, seed, t, right,
                   down);
     orc_label_bfs(Lx, Ly, per_x, per_y, right, down, label, queue);
-    orc_flip_f16(Lx, Ly, theta_bits, label, seed, t, c32, NULL);
+    long flipped = orc_flip_f16(Lx, Ly, theta_bits, label, seed, t, c32, NULL);
     if (obs) {
       orc_sums sm;
       orc_sums_f16(Lx, Ly, per_x, per_y, theta_bits, &sm);
       orc_derive(&sm, beta, &obs[s]);
+      obs[s].flipped = (double)flipped;
     }
   }
 }
@@ -677,11 +680,12 @@ void orc_sw_run_u16(int Lx, int Ly, int per_x, int per_y, uint16_t *q,
     orc_axis_u16(seed, t, ax, &cq);
     orc_bonds_u16(Lx, Ly, per_x, per_y, q, beta, seed, t, right, down);
     orc_label_bfs(Lx, Ly, per_x, per_y, right, down, label, queue);
-    orc_flip_u16(Lx, Ly, q, label, seed, t, cq, NULL);
+    long flipped = orc_flip_u16(Lx, Ly, q, label, seed, t, cq, NULL);
     if (obs) {
       orc_sums sm;
       orc_sums_u16(Lx, Ly, per_x, per_y, q, &sm);
       orc_derive(&sm, beta, &obs[s]);
+      obs[s].flipped = (double)flipped;
     }
   }
 }
@@ -707,6 +711,159 @@ void orc_pcc_run_f32(int L, float *theta, double *beta, double target,
       *blk_count = 0;
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wolff single-cluster update (Sec. 2 names Wolff's single-cluster          */
+/* algorithm beside SW).  Update t uses the axis and the bond random numbers */
+/* of SW sweep t; its seed site comes from word 2 of the AXIS draw.  The     */
+/* cluster is grown the way the single-cluster algorithm grows it: a         */
+/* breadth-first search from the seed that tests each bond on the cluster's  */
+/* boundary as it meets it, with the same FP64 rule and the same random word */
+/* that the SW bonds use.  The cluster is always reflected.                  */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_seed_site(uint64_t seed, uint32_t t, uint64_t n) {
+  uint32_t w[4];
+  philox_draw(seed, 0u, 0u, t, ORC_DOM_AXIS, w);
+  return ((uint64_t)w[2] * n) >> 32; /* uniform over 0 .. n-1 (n <= 2^32) */
+}
+
+static int left_of(int Lx, int per_x, uint64_t i, uint64_t *j) {
+  uint64_t x = i % (uint64_t)Lx;
+  if (x > 0) { *j = i - 1; return 1; }
+  if (!per_x) return 0;
+  *j = i + (uint64_t)Lx - 1;
+  return 1;
+}
+
+static int up_of(int Lx, int Ly, int per_y, uint64_t i, uint64_t *j) {
+  uint64_t y = i / (uint64_t)Lx;
+  if (y > 0) { *j = i - (uint64_t)Lx; return 1; }
+  if (!per_y) return 0;
+  *j = i + (uint64_t)Lx * (uint64_t)(Ly - 1);
+  return 1;
+}
+
+/* Is the right (dir 0) or down (dir 1) bond of site `owner` active?  The
+ * same test as bonds_generic, for one bond. */
+static int bond_active(int Lx, int Ly, int per_x, int per_y, const double *ang,
+                       double cphi, double sphi, double beta, uint64_t seed,
+                       uint32_t t, uint64_t owner, int dir) {
+  uint64_t j;
+  int ok = dir == 0 ? right_of(Lx, Ly, per_x, owner, &j)
+                    : down_of(Lx, Ly, per_y, owner, &j);
+  if (!ok) return 0;
+  uint32_t w[4];
+  philox_draw(seed, (uint32_t)owner, (uint32_t)(owner >> 32), t, ORC_DOM_BOND,
+              w);
+  double ai = projection(ang[owner], cphi, sphi);
+  double aj = projection(ang[j], cphi, sphi);
+  double p = bond_probability(ai, aj, beta);
+  double u = uniform_open(dir == 0 ? w[0] : w[1]);
+  return (ai * aj > 0.0) && (u < p);
+}
+
+long orc_wolff_cluster(int Lx, int Ly, int per_x, int per_y, const double *ang,
+                       double cphi, double sphi, double beta, uint64_t seed,
+                       uint32_t t, uint64_t i0, uint8_t *in_cluster,
+                       uint32_t *queue) {
+  uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
+  memset(in_cluster, 0, n);
+  uint64_t head = 0, tail = 0;
+  in_cluster[i0] = 1;
+  queue[tail++] = (uint32_t)i0;
+  while (head < tail) {
+    uint64_t i = queue[head++];
+    for (int k = 0; k < 4; ++k) {
+      /* the bond to each neighbour, named by its owner (the left or upper
+       * site) and direction */
+      uint64_t owner = i, other;
+      int dir = k & 1;
+      int ok;
+      if (k == 0) ok = right_of(Lx, Ly, per_x, i, &other);
+      else if (k == 1) ok = down_of(Lx, Ly, per_y, i, &other);
+      else if (k == 2) { ok = left_of(Lx, per_x, i, &other); owner = other; }
+      else { ok = up_of(Lx, Ly, per_y, i, &other); owner = other; }
+      if (!ok || in_cluster[other]) continue;
+      if (bond_active(Lx, Ly, per_x, per_y, ang, cphi, sphi, beta, seed, t,
+                      owner, dir)) {
+        in_cluster[other] = 1;
+        queue[tail++] = (uint32_t)other;
+      }
+    }
+  }
+  return (long)tail;
+}
+
+/* n Wolff updates t0 .. t0+n-1 of angles in storage format dtype (0 FP32,
+ * 1 FP16 bits, 2 u16), recording the configuration after each. */
+static void wolff_run(int dtype, int Lx, int Ly, int per_x, int per_y,
+                      void *theta, double beta, uint64_t seed, uint32_t t0,
+                      uint32_t n, uint8_t *in_cluster, uint32_t *queue,
+                      orc_obs *obs) {
+  uint64_t N = (uint64_t)Lx * (uint64_t)Ly;
+  for (uint32_t s = 0; s < n; ++s) {
+    uint32_t t = t0 + s;
+    double ax[4];
+    float c32 = 0.0f;
+    uint16_t cq = 0;
+    double *ang;
+    if (dtype == 2) {
+      orc_axis_u16(seed, t, ax, &cq);
+      ang = widen_u16((const uint16_t *)theta, N);
+    } else {
+      orc_axis(seed, t, ax, &c32);
+      ang = dtype == 0 ? widen_f32((const float *)theta, N)
+                       : widen_f16((const uint16_t *)theta, N);
+    }
+    uint64_t i0 = orc_seed_site(seed, t, N);
+    long size = orc_wolff_cluster(Lx, Ly, per_x, per_y, ang, ax[1], ax[2],
+                                  beta, seed, t, i0, in_cluster, queue);
+    free(ang);
+    for (uint64_t i = 0; i < N; ++i) {
+      if (!in_cluster[i]) continue;
+      if (dtype == 0) {
+        float *th = (float *)theta;
+        th[i] = wrap_f32(c32 - th[i]);
+      } else if (dtype == 1) {
+        uint16_t *hb = (uint16_t *)theta;
+        hb[i] = store_angle_f16(wrap_f32(c32 - half_bits_to_float(hb[i])));
+      } else {
+        uint16_t *q = (uint16_t *)theta;
+        q[i] = (uint16_t)(((uint32_t)cq + 65536u - (uint32_t)q[i]) & 0xFFFFu);
+      }
+    }
+    if (obs) {
+      orc_sums sm;
+      if (dtype == 0) orc_sums_f32(Lx, Ly, per_x, per_y, (const float *)theta, &sm);
+      else if (dtype == 1) orc_sums_f16(Lx, Ly, per_x, per_y, (const uint16_t *)theta, &sm);
+      else orc_sums_u16(Lx, Ly, per_x, per_y, (const uint16_t *)theta, &sm);
+      orc_derive(&sm, beta, &obs[s]);
+      obs[s].flipped = (double)size;
+    }
+  }
+}
+
+void orc_wolff_run_f32(int Lx, int Ly, int per_x, int per_y, float *theta,
+                       double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                       uint8_t *in_cluster, uint32_t *queue, orc_obs *obs) {
+  wolff_run(0, Lx, Ly, per_x, per_y, theta, beta, seed, t0, n, in_cluster,
+            queue, obs);
+}
+
+void orc_wolff_run_f16(int Lx, int Ly, int per_x, int per_y,
+                       uint16_t *theta_bits, double beta, uint64_t seed,
+                       uint32_t t0, uint32_t n, uint8_t *in_cluster,
+                       uint32_t *queue, orc_obs *obs) {
+  wolff_run(1, Lx, Ly, per_x, per_y, theta_bits, beta, seed, t0, n,
+            in_cluster, queue, obs);
+}
+
+void orc_wolff_run_u16(int Lx, int Ly, int per_x, int per_y, uint16_t *q,
+                       double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                       uint8_t *in_cluster, uint32_t *queue, orc_obs *obs) {
+  wolff_run(2, Lx, Ly, per_x, per_y, q, beta, seed, t0, n, in_cluster, queue,
+            obs);
 }
 
 /* ------------------------------------------------------------------------ */

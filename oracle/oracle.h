@@ -80,6 +80,7 @@ typedef struct {
   double chik;             /* (|F(kx)|^2 + |F(ky)|^2) / (2N): the
                               configuration's chi at the smallest nonzero
                               wave vector, averaged over x and y (Eq. (9)) */
+  double flipped;          /* sites the update reflected (0 from derive)   */
 } orc_obs;
 
 /* ---- Philox4x32-10 ------------------------------------------------------ */
@@ -194,6 +195,31 @@ void orc_pcc_run_f32(int L, float *theta, double *beta, double target,
                      double *blk_acc, uint32_t *blk_count, uint8_t *right,
                      uint8_t *down, uint32_t *label, uint32_t *queue,
                      orc_obs *obs);
+
+/* ---- Wolff single-cluster updates (Sec. 2 names the algorithm) -------- */
+/* Update t: the axis and bond random numbers of SW sweep t, seed site
+ * i0 = (word 2 of the AXIS draw * n) >> 32.  The cluster of i0 is grown by a
+ * breadth-first search that tests each boundary bond with the SW bond rule
+ * when it meets it, and is always reflected. */
+uint64_t orc_seed_site(uint64_t seed, uint32_t t, uint64_t n);
+/* in_cluster: N bytes (1 = in the cluster), queue: N uint32.  ang: angles in
+ * FP64, (cphi, sphi) the axis.  Returns the cluster size. */
+long orc_wolff_cluster(int Lx, int Ly, int per_x, int per_y, const double *ang,
+                       double cphi, double sphi, double beta, uint64_t seed,
+                       uint32_t t, uint64_t i0, uint8_t *in_cluster,
+                       uint32_t *queue);
+/* n updates t0 .. t0+n-1 in place; obs (may be NULL) gets one record per
+ * update with flipped = the cluster size. */
+void orc_wolff_run_f32(int Lx, int Ly, int per_x, int per_y, float *theta,
+                       double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                       uint8_t *in_cluster, uint32_t *queue, orc_obs *obs);
+void orc_wolff_run_f16(int Lx, int Ly, int per_x, int per_y,
+                       uint16_t *theta_bits, double beta, uint64_t seed,
+                       uint32_t t0, uint32_t n, uint8_t *in_cluster,
+                       uint32_t *queue, orc_obs *obs);
+void orc_wolff_run_u16(int Lx, int Ly, int per_x, int per_y, uint16_t *q,
+                       double beta, uint64_t seed, uint32_t t0, uint32_t n,
+                       uint8_t *in_cluster, uint32_t *queue, orc_obs *obs);
 
 /* Metropolis single-spin-flip sweeps (typewriter order, FP64 angles), an
  * independent sampler used only to cross-check the cluster chain. */
