@@ -239,6 +239,8 @@ def run_ours(args):
         if args.exact_report:
             out["exact_mode"] = exact_report(xy, L, beta, args)
             out["storage"] = storage_report(xy, L, beta, args)
+            out["wolff"] = wolff_report(xy, L, beta, args)
+            out["wolff"]["sw_reflected_sites_per_ns"] = round(0.5 * value / ws, 3)
         if args.big and ws == 1:
             out["l65536"] = run_big(xy, args)
         if args.batched:
@@ -326,6 +328,34 @@ def storage_report(xy, L, beta, args):
                    "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in kt.items()}}
         lat.close()
     return out
+
+
+def wolff_report(xy, L, beta, args):
+    """Wolff single-cluster updates at the benchmark size: update rate, mean
+    cluster fraction and reflected sites per ns, beside the SW sweep's
+    (which reflects N/2 sites on average)."""
+    import torch
+
+    lat = xy.Lattice(L, beta, seed=4545, tile_y=args.tile_y, exact=bool(args.exact),
+                     update="wolff", record_cap=4096)
+    lat.sweep(20)
+    torch.cuda.synchronize()
+    lat.measure()
+    n = max(20, min(400, args.steps))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.sweep(n)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    frac = float(lat.measure()["flipped"].mean()) / (L * L)
+    lat.close()
+    return {"updates_per_s": round(1e3 / ms, 1), "ms_per_update": round(ms, 5),
+            "mean_cluster_fraction": round(frac, 4),
+            "reflected_sites_per_ns": round(frac * L * L / (ms * 1e6), 3),
+            "how": f"L={L}, beta={beta}, {n} updates after 20; cluster found by the sweep's "
+                   "bond and label kernels (one launch set per update)"}
 
 
 def run_big(xy, args):

@@ -78,6 +78,21 @@ typedef enum { XY_F32 = 0, XY_F16 = 1, XY_U16 = 2 } xy_angle_t;
  * bonds). */
 typedef enum { XY_THR_F32 = 0, XY_THR_F64 = 1 } xy_thr_t;
 
+/* What one step (xy_sweep, xy_pcc_step, an engine step) does.
+ * XY_UPDATE_SW: one Swendsen-Wang sweep with Wolff's embedding.  Every
+ *   cluster of the bond configuration is reflected with probability 1/2.
+ * XY_UPDATE_WOLFF: one Wolff single-cluster update (Sec. 2 names the
+ *   algorithm).  Step t uses the axis and the bond random numbers of SW
+ *   sweep t.  Its seed site is i0 = (w2 * N) >> 32, with w2 word 2 of the
+ *   step's AXIS draw.  Only the cluster containing i0 is reflected, and it
+ *   always is.  That cluster has the same law as the one the single-cluster
+ *   algorithm grows from i0 by testing bonds one at a time, because the
+ *   bonds are independent.  The GPU finds it with the same bond and label
+ *   kernels as a sweep, so a step costs about as much as a sweep and
+ *   reflects on average <cluster size> sites instead of N/2.  Records give
+ *   the cluster size in `flipped`. */
+typedef enum { XY_UPDATE_SW = 0, XY_UPDATE_WOLFF = 1 } xy_update_t;
+
 typedef struct {
   uint32_t L;              /* linear size, 2 .. 65536 (N = L*L <= 2^32)     */
   uint32_t tile_y;         /* labeling tile height: 16, 32, 64 or 128;
@@ -92,7 +107,7 @@ typedef struct {
                               0 = 4096                                      */
   uint32_t measure_xi;     /* 1: also record chik (second-moment correlation
                               length, Eqs. (8)-(9)); 0: chik = 0           */
-  uint32_t reserved;       /* must be 0                                     */
+  uint32_t update;         /* xy_update_t                                   */
 } xy_config;
 
 /* Observables of the configuration after one sweep (FP64).  N = L*L.
@@ -110,11 +125,15 @@ typedef struct {
  *            chi(k) at the smallest wave vector (Eq. (9), read as the
  *            thermal average of |F|^2).  With chi0 = N m2,
  *            xi_2nd = sqrt(<chi0>/<chik> - 1) / (2 sin(pi/L))   (Eq. (8)).
- *            Recorded only when the config sets measure_xi, else 0.    */
+ *            Recorded only when the config sets measure_xi, else 0.
+ *   flipped = Wolff updates: the number of sites reflected (the cluster
+ *            size); 0 for SW sweeps (not counted there, to keep the sweep's
+ *            observable kernel lean)                                      */
 typedef struct {
   double energy_per_site, m2, mx, my, ex, sx, ey, sy, upsilon, beta;
   uint64_t sweep;
   double chik;
+  uint64_t flipped;
 } xy_obs;
 
 /* Helicity-modulus PCC (Sec. 2): after every `block` sweeps, with

@@ -27,6 +27,17 @@ XY_F32, XY_F16, XY_U16 = 0, 1, 2
 DTYPES = {"f32": (XY_F32, np.float32), "f16": (XY_F16, np.float16), "u16": (XY_U16, np.uint16)}
 
 
+XY_UPDATE_SW, XY_UPDATE_WOLFF = 0, 1
+
+
+def _update(name: str) -> int:
+    """'sw': Swendsen-Wang sweep; 'wolff': Wolff single-cluster update."""
+    codes = {"sw": XY_UPDATE_SW, "wolff": XY_UPDATE_WOLFF}
+    if name not in codes:
+        raise ValueError("update must be 'sw' or 'wolff'")
+    return codes[name]
+
+
 def _dtype(name: str):
     if name not in DTYPES:
         raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
@@ -60,7 +71,7 @@ class xy_config(ctypes.Structure):
                 ("beta", ctypes.c_double), ("angle_dtype", ctypes.c_int32),
                 ("threshold_mode", ctypes.c_int32), ("start", ctypes.c_int32),
                 ("record_cap", ctypes.c_uint32), ("measure_xi", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("update", ctypes.c_uint32)]
 
 
 OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy", "upsilon", "beta")
@@ -68,11 +79,12 @@ OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy", "upsi
 
 class xy_obs(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_double) for n in OBS_FIELDS] + [("sweep", ctypes.c_uint64)]
-                + [("chik", ctypes.c_double)])
+                + [("chik", ctypes.c_double), ("flipped", ctypes.c_uint64)])
 
 
 OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS] + [("sweep", np.uint64),
-                                                             ("chik", np.float64)])
+                                                             ("chik", np.float64),
+                                                             ("flipped", np.uint64)])
 assert OBS_DTYPE.itemsize == ctypes.sizeof(xy_obs)
 
 
@@ -218,7 +230,8 @@ class Lattice:
 
     def __init__(self, L: int, beta: float, seed: int, *, dtype: str = "f32",
                  exact: bool = True, start: str = "random", tile_y: int = 0,
-                 record_cap: int = 0, measure_xi: bool = False, stream=None):
+                 record_cap: int = 0, measure_xi: bool = False, update: str = "sw",
+                 stream=None):
         import torch  # plumbing: device memory and streams
 
         self.L = int(L)
@@ -228,7 +241,7 @@ class Lattice:
                              angle_dtype=code,
                              threshold_mode=XY_THR_F64 if exact else XY_THR_F32,
                              start=0 if start == "random" else 1, record_cap=record_cap,
-                             measure_xi=1 if measure_xi else 0)
+                             measure_xi=1 if measure_xi else 0, update=_update(update))
         self.nbytes = xy_workspace_size(self.cfg)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
@@ -354,12 +367,12 @@ class Engine:
         self.L = {}
 
     def config(self, L: int, beta: float, seed: int, start: str = "random",
-               record_cap: int = 0, measure_xi: bool = False) -> xy_config:
+               record_cap: int = 0, measure_xi: bool = False, update: str = "sw") -> xy_config:
         return xy_config(L=L, tile_y=self.tile_y, seed=seed, beta=beta,
                          angle_dtype=_dtype(self.dtype)[0],
                          threshold_mode=XY_THR_F64 if self.exact else XY_THR_F32,
                          start=0 if start == "random" else 1, record_cap=record_cap,
-                         measure_xi=1 if measure_xi else 0)
+                         measure_xi=1 if measure_xi else 0, update=_update(update))
 
     @staticmethod
     def footprint(cfg: xy_config) -> int:

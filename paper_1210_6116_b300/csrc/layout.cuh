@@ -47,8 +47,8 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
     return layout_fail(XY_EINVAL, "threshold_mode must be XY_THR_F32 or XY_THR_F64");
   if (c->start != 0 && c->start != 1)
     return layout_fail(XY_EINVAL, "start must be 0 (random) or 1 (ordered)");
-  if (c->measure_xi > 1 || c->reserved != 0)
-    return layout_fail(XY_EINVAL, "measure_xi must be 0 or 1 and reserved 0");
+  if (c->measure_xi > 1 || c->update > XY_UPDATE_WOLFF)
+    return layout_fail(XY_EINVAL, "measure_xi must be 0 or 1, update XY_UPDATE_SW or XY_UPDATE_WOLFF");
   const uint32_t ty = c->tile_y ? c->tile_y : default_tile_y(c->L);
   if (!tile_ok(ty)) return layout_fail(XY_EINVAL, "tile_y must be 16, 32, 64 or 128");
   lo->L = c->L;
@@ -101,6 +101,7 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.dplane = reinterpret_cast<uint32_t *>(ws + lo.off_dplane);
   d.coin = reinterpret_cast<uint32_t *>(ws + lo.off_coin);
   d.xi = cfg->measure_xi ? 1u : 0u;
+  d.wolff = cfg->update == XY_UPDATE_WOLFF ? 1u : 0u;
   d.wave = reinterpret_cast<const float2 *>(ws + lo.off_wave);
   d.acc = reinterpret_cast<long long *>(ws + lo.off_acc);
   d.st = reinterpret_cast<DevState *>(ws + lo.off_state);

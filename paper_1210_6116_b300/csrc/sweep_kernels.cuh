@@ -41,7 +41,8 @@ namespace xyk {
 constexpr int kThreads = 256;          // 8 warps per tile CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kSlots = 64;             // accumulator slots per lattice
-constexpr int kAccStride = 16;         // int64 per slot (6, or 14 with xi)
+constexpr int kAccStride = 16;         // int64 per slot (6, or 14 with xi; [15] flips)
+constexpr int kFlipSlot = 15;          // slot entry counting the reflected sites
 constexpr uint32_t kFindCap = 1u << 22;  // bound on any global find / union loop
 
 // error bits recorded in DevState::err
@@ -56,6 +57,7 @@ struct ObsRecord {  // identical layout to xy_obs
   double energy_per_site, m2, mx, my, ex, sx, ey, sy, upsilon, beta;
   uint64_t sweep;
   double chik;
+  uint64_t flipped;
 };
 
 struct DevState {
@@ -78,14 +80,16 @@ struct DevState {
   uint64_t rec_count;
   // diagnostics
   unsigned long long n_fp64, n_fp32_wrong;
-  uint32_t err, pad2;
+  uint32_t err;
+  uint32_t seed_site;  // Wolff update t: the site whose cluster is reflected
 };
 
 struct LatDesc {
   uint32_t L, ntx, nty, ntiles;
   uint32_t key0, key1, rec_cap, ragged;
   uint64_t Lmagic;  // ceil(2^64 / L): x / L == umul64hi(x, Lmagic) for x < 2^32
-  uint32_t xi, pad0;  // 1: accumulate the Fourier sums of chik
+  uint32_t xi;     // 1: accumulate the Fourier sums of chik
+  uint32_t wolff;  // 1: Wolff single-cluster update (reflect the seed's cluster)
   const float2 *wave;  // [L]: (cos, sin)(2 pi x / L), used when xi
   void *theta[2];
   uint32_t *label;
@@ -745,13 +749,17 @@ constexpr size_t flip_smem() {
 // tile root, or its root when k_compress jumped it), then that entry's entry,
 // which k_compress has made the root (every merged tile root is jumped until
 // its parent is a root; an unmerged one is its own entry).
-template <int TY, typename AT, bool LABELS_ONLY, bool XI = false>
-__global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need registers
+// EXT: the extended instantiation, for lattice tables where some lattice
+// measures chik (d.xi) or runs Wolff updates (d.wolff); each lattice still
+// takes only what its own flags ask for.  The lean one does neither and
+// keeps its registers (launch bounds 5 CTAs/SM; EXT needs 4).
+template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false>
+__global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
                    uint32_t nwork) {
   constexpr int B = TY / kWarps;
-  __shared__ long long red[kWarps][XI ? 14 : 6];
+  __shared__ long long red[kWarps][EXT ? 15 : 6];  // EXT: 14 sums + flip count
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
@@ -811,14 +819,29 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
         __stcg(lab + static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane, l[k]);
     }
     if (LABELS_ONLY) continue;
-    // round 4: coins of the roots
-    uint32_t f[B + 1];
+    // round 4: which sites reflect.  SW: the coin of the site's root.
+    // Wolff: the sites of the seed site's cluster, whose root is the entry's
+    // entry of the seed like any other site's (whether or not this kernel
+    // has already rewritten those entries: both reads give the root)
+    uint32_t f[B + 1], fc;
+    int nflip = 0;  // Wolff: reflected sites of the band (warp-uniform)
+    if (EXT && d.wolff) {
+      const uint32_t r0 = __ldcg(lab + __ldcg(lab + st->seed_site));
 #pragma unroll
-    for (int k = 0; k <= B; ++k)
-      f[k] = (static_cast<uint32_t>(k) <= nb && col_ok)
-                 ? (__ldg(d.coin + (l[k] >> 5)) >> (l[k] & 31u)) & 1u
-                 : 0u;
-    const uint32_t fc = vc ? (__ldg(d.coin + (lc >> 5)) >> (lc & 31u)) & 1u : 0u;
+      for (int k = 0; k <= B; ++k)
+        f[k] = (static_cast<uint32_t>(k) <= nb && col_ok && l[k] == r0) ? 1u : 0u;
+      fc = (vc && lc == r0) ? 1u : 0u;
+#pragma unroll
+      for (int k = 0; k < B; ++k)
+        nflip += __popc(__ballot_sync(0xFFFFFFFFu, f[k] && static_cast<uint32_t>(k) < nb));
+    } else {
+#pragma unroll
+      for (int k = 0; k <= B; ++k)
+        f[k] = (static_cast<uint32_t>(k) <= nb && col_ok)
+                   ? (__ldg(d.coin + (l[k] >> 5)) >> (l[k] & 31u)) & 1u
+                   : 0u;
+      fc = vc ? (__ldg(d.coin + (lc >> 5)) >> (lc & 31u)) & 1u : 0u;
+    }
     // reflection, stores, and cos/sin of the new angles
     float co[B + 1], sn[B + 1];
 #pragma unroll
@@ -837,13 +860,13 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
     sin_cos<AT>(fc ? reflect<AT>(tc, c32) : tc, &sc, &cc);
     // observable terms of the band's own sites (with d.xi also the Fourier
     // sums of chik: s(r) times (cos, sin)(2 pi x / L) and (2 pi y / L))
-    constexpr int NV = XI ? 14 : 6;
+    constexpr int NV = EXT ? 14 : 6;
     int acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0;
-    const bool xi = XI && d.xi != 0u;
+    const bool xi = EXT && d.xi != 0u;
     float2 wx = make_float2(0.0f, 0.0f);
-    if constexpr (XI) {
+    if constexpr (EXT) {
       if (xi && col_ok) wx = __ldg(d.wave + g.x0 + lane);
     }
 #pragma unroll
@@ -865,7 +888,7 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
         acc[3] += fix22(fmaf(si, cr, -(ci * sr)));
         acc[4] += fix22(fmaf(ci, cd, si * sd));
         acc[5] += fix22(fmaf(si, cd, -(ci * sd)));
-        if constexpr (XI) {
+        if constexpr (EXT) {
           if (xi) {
             const float2 wy = __ldg(d.wave + g.y0 + r0 + k);
             acc[NV - 8] += fix22(ci * wx.x);
@@ -894,6 +917,7 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+      if constexpr (EXT) red[warp][NV] = nflip;
     }
     __syncthreads();
     if (threadIdx.x < static_cast<unsigned>(nv)) {
@@ -904,6 +928,16 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
                     d.acc + (tile % kSlots) * kAccStride + threadIdx.x),
                 static_cast<unsigned long long>(sum));
     }
+    if constexpr (EXT) {
+      if (threadIdx.x == 32u && d.wolff) {
+        long long sum = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) sum += red[w][NV];
+        atomicAdd(reinterpret_cast<unsigned long long *>(
+                      d.acc + (tile % kSlots) * kAccStride + kFlipSlot),
+                  static_cast<unsigned long long>(sum));
+      }
+    }
     __syncthreads();
   }
 }
@@ -912,8 +946,11 @@ __global__ void __launch_bounds__(kThreads, XI ? 4 : 5)  // XI: 8 more sums need
 // axis of sweep t and the FP32 constants derived from it and beta
 // ---------------------------------------------------------------------------
 __device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta,
-                                        uint32_t k0, uint32_t k1) {
+                                        uint32_t k0, uint32_t k1, uint32_t L) {
   const Words4 w = philox4x32_10(0u, 0u, t, kDomAxis, k0, k1);
+  // seed site of a Wolff update: word 2 scaled to 0 .. N-1 (N = L^2 <= 2^32)
+  st->seed_site = static_cast<uint32_t>(
+      (static_cast<uint64_t>(w.w2) * (static_cast<uint64_t>(L) * L)) >> 32);
   const uint64_t bits = (static_cast<uint64_t>(w.w0) << 32) | w.w1;
   double s, c;
   float c32;
@@ -954,7 +991,7 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
   const LatDesc &d = descs[rep];
   DevState *st = d.st;
   const int lane = threadIdx.x;
-  long long v[14];
+  long long v[14], nf = 0;
 #pragma unroll
   for (int k = 0; k < 14; ++k) v[k] = 0;
   for (int s = lane; s < kSlots; s += 32) {
@@ -963,6 +1000,8 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
       v[k] += d.acc[s * kAccStride + k];
       d.acc[s * kAccStride + k] = 0;
     }
+    nf += d.acc[s * kAccStride + kFlipSlot];
+    d.acc[s * kAccStride + kFlipSlot] = 0;
   }
 #pragma unroll
   for (int k = 0; k < 14; ++k) {
@@ -970,6 +1009,8 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
     for (int off = 16; off > 0; off >>= 1)
       v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nf += __shfl_down_sync(0xFFFFFFFFu, nf, off);
   if (lane != 0) return;
   const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
   double S[14];
@@ -992,6 +1033,7 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
 #pragma unroll
   for (int k = 6; k < 14; ++k) f2 += S[k] * S[k];
   o.chik = f2 / (2.0 * n);  // 0 unless the lattice measures xi
+  o.flipped = static_cast<uint64_t>(nf);
   d.rec[st->rec_count % d.rec_cap] = o;
   st->rec_count += 1;
   double nb = beta;
@@ -1009,7 +1051,7 @@ static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nr
     st->pcc_k += 1;
   }
   st->cur ^= 1u;
-  set_sweep_params(st, st->t + 1u, nb, d.key0, d.key1);
+  set_sweep_params(st, st->t + 1u, nb, d.key0, d.key1, d.L);
 }
 
 // ---------------------------------------------------------------------------
@@ -1063,7 +1105,7 @@ static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   st->n_fp64 = 0;
   st->n_fp32_wrong = 0;
   st->err = 0;
-  set_sweep_params(st, 0u, beta, d.key0, d.key1);
+  set_sweep_params(st, 0u, beta, d.key0, d.key1, d.L);
 }
 
 static __global__ void k_set_pcc(DevState *st, uint32_t on, double target,

@@ -99,7 +99,7 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   if ((e = mark(h)) != cudaSuccess) return e;
   k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   if ((e = mark(h)) != cudaSuccess) return e;
-  if (h->desc.xi)
+  if (h->desc.xi || h->desc.wolff)  // chik sums or Wolff: the extended K4
     k_flip_measure<TY, AT, false, true>
         <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
   else

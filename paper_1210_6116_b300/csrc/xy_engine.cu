@@ -57,14 +57,14 @@ struct Slot {
 
 template <int TY, typename AT, bool EXACT>
 void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uint32_t nw,
-                bool xi, cudaStream_t s) {
+                bool ext, cudaStream_t s) {
   k_bond_label<TY, AT, EXACT, false>
       <<<nw, kThreads, bond_label_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
   k_merge<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
   k_compress<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
-  if (xi)  // some lattice measures xi; the others skip it by their own flag
+  if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
     k_flip_measure<TY, AT, false, true><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   else
     k_flip_measure<TY, AT, false, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
@@ -73,12 +73,12 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
 
 template <typename AT, bool EXACT>
 void launch_ty(uint32_t TY, const LatDesc *descs, const uint32_t *prefix, uint32_t nrep,
-               uint32_t nw, bool xi, cudaStream_t s) {
+               uint32_t nw, bool ext, cudaStream_t s) {
   switch (TY) {
-    case 16: launch_all<16, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
-    case 32: launch_all<32, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
-    case 64: launch_all<64, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
-    default: launch_all<128, AT, EXACT>(descs, prefix, nrep, nw, xi, s); break;
+    case 16: launch_all<16, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
+    case 32: launch_all<32, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
+    case 64: launch_all<64, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
+    default: launch_all<128, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
   }
 }
 
@@ -108,18 +108,18 @@ size_t table_bytes(uint32_t max_slots) {
 }
 
 void launch_table(xy_engine *e, cudaStream_t s) {
-  bool xi = false;
-  for (const LatDesc &d : e->h_descs) xi = xi || d.xi;
+  bool ext = false;
+  for (const LatDesc &d : e->h_descs) ext = ext || d.xi || d.wolff;
   const bool ex = e->thr == XY_THR_F64;
   if (e->dtype == XY_F32) {
-    if (ex) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
-    else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    if (ex) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
+    else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
   } else if (e->dtype == XY_F16) {
-    if (ex) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
-    else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    if (ex) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
+    else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
   } else {
-    if (ex) launch_ty<uint16_t, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
-    else launch_ty<uint16_t, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, xi, s);
+    if (ex) launch_ty<uint16_t, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
+    else launch_ty<uint16_t, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
   }
 }
 

@@ -30,9 +30,11 @@ EPS_SITE = 2.4e-7
 EPS_WAVE = 3.6e-7
 
 
-def obs_close(g: dict, o: dict, N: int, beta: float, xi: bool = False):
+def obs_close(g: dict, o: dict, N: int, beta: float, xi: bool = False, flips: bool = False):
     """Return a list of (field, gpu, oracle, tol) that violate the tolerance.
-    xi: the GPU lattice measures chik; otherwise its chik must be exactly 0."""
+    xi: the GPU lattice measures chik; otherwise its chik must be exactly 0.
+    flips: the GPU counts reflected sites (Wolff), compared exactly with the
+    oracle's count; otherwise (SW) the count must be 0."""
     bad = []
 
     def chk(k, tol):
@@ -57,6 +59,11 @@ def obs_close(g: dict, o: dict, N: int, beta: float, xi: bool = False):
         bad.append(("chik", g["chik"], 0.0, 0.0))
     if g["beta"] != o["beta"]:
         bad.append(("beta", g["beta"], o["beta"], 0.0))
+    if flips:
+        if g["flipped"] != o["flipped"]:
+            bad.append(("flipped", g["flipped"], o["flipped"], 0.0))  # a count: exact
+    elif g.get("flipped", 0.0) != 0.0:
+        bad.append(("flipped", g["flipped"], 0.0, 0.0))
     return bad
 
 
