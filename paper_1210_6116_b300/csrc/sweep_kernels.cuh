@@ -88,6 +88,7 @@ struct LatDesc {
   uint32_t L, ntx, nty, ntiles;
   uint32_t key0, key1, rec_cap, ragged;
   uint64_t Lmagic;  // ceil(2^64 / L): x / L == umul64hi(x, Lmagic) for x < 2^32
+  double inv_n;     // 1 / L^2
   uint32_t xi;     // 1: accumulate the Fourier sums of chik
   uint32_t wolff;  // 1: Wolff single-cluster update (reflect the seed's cluster)
   const float2 *wave;  // [L]: (cos, sin)(2 pi x / L), used when xi
@@ -945,38 +946,54 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
 // ---------------------------------------------------------------------------
 // axis of sweep t and the FP32 constants derived from it and beta
 // ---------------------------------------------------------------------------
-__device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta,
-                                        uint32_t k0, uint32_t k1, uint32_t L) {
+// The part of sweep t's parameters that does not depend on beta: the axis,
+// the reflection constant and the Wolff seed site.
+struct Axis {
+  double c, s;         // cos, sin of the axis angle (FP64)
+  float c32;           // reflection constant (u16: Cq)
+  uint32_t seed_site;  // Wolff: the site whose cluster is reflected
+};
+
+__device__ inline Axis draw_axis(uint32_t quant, uint32_t t, uint32_t k0, uint32_t k1,
+                                 uint32_t L) {
   const Words4 w = philox4x32_10(0u, 0u, t, kDomAxis, k0, k1);
+  Axis a;
   // seed site of a Wolff update: word 2 scaled to 0 .. N-1 (N = L^2 <= 2^32)
-  st->seed_site = static_cast<uint32_t>(
+  a.seed_site = static_cast<uint32_t>(
       (static_cast<uint64_t>(w.w2) * (static_cast<uint64_t>(L) * L)) >> 32);
   const uint64_t bits = (static_cast<uint64_t>(w.w0) << 32) | w.w1;
-  double s, c;
-  float c32;
-  if (st->quant) {
+  if (quant) {
     // u16 angles: the axis on the reflection grid, phi_q = pi m / 65536 with
     // m = phi mod pi floored to the grid, and Cq = m + 32768 (mod 65536), so
     // that pi + 2 phi_q = Cq 2pi / 65536 and the flip is q -> Cq - q
     const uint32_t m = static_cast<uint32_t>(bits >> 47) & 0xFFFFu;
-    sincospi(static_cast<double>(m) * 0x1p-16, &s, &c);
-    c32 = static_cast<float>((m + 32768u) & 0xFFFFu);
+    sincospi(static_cast<double>(m) * 0x1p-16, &a.s, &a.c);
+    a.c32 = static_cast<float>((m + 32768u) & 0xFFFFu);
   } else {
     const double u = static_cast<double>(bits >> 11) * 0x1p-53;
     const double phi = __dmul_rn(6.283185307179586, u);
-    sincos(phi, &s, &c);
-    const double C = fmod(__dadd_rn(3.141592653589793, __dmul_rn(2.0, phi)),
-                          6.283185307179586);
-    c32 = __double2float_rn(C);
-    if (c32 >= two_pi_f()) c32 = 0.0f;
+    sincos(phi, &a.s, &a.c);
+    // C = (pi + 2 phi) mod 2pi.  pi + 2 phi lies in [pi, 5pi) and both
+    // subtractions are exact (Sterbenz), so this is fmod's result exactly.
+    const double two_pi = 6.283185307179586;
+    double C = __dadd_rn(3.141592653589793, __dmul_rn(2.0, phi));
+    if (C >= 2.0 * two_pi) C = __dsub_rn(C, 2.0 * two_pi);
+    else if (C >= two_pi) C = __dsub_rn(C, two_pi);
+    a.c32 = __double2float_rn(C);
+    if (a.c32 >= two_pi_f()) a.c32 = 0.0f;
   }
+  return a;
+}
+
+__device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta, const Axis &a) {
   st->t = t;
   st->beta = beta;
-  st->cphi = c;
-  st->sphi = s;
-  st->cphi32 = __double2float_rn(c);
-  st->sphi32 = __double2float_rn(s);
-  st->c32 = c32;
+  st->cphi = a.c;
+  st->sphi = a.s;
+  st->cphi32 = __double2float_rn(a.c);
+  st->sphi32 = __double2float_rn(a.s);
+  st->c32 = a.c32;
+  st->seed_site = a.seed_site;
   st->beta2_32 = __double2float_rn(2.0 * beta);
   // band half-width: 4x the error bound of the FP32 evaluation of u - p;
   // u16 adds <= 4.2e-7 per projection for the FP32 angle q 2pi_f 2^-16
@@ -984,74 +1001,92 @@ __device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta,
   st->eps = __double2float_rn(4.0 * (2.0 * beta * dx + 3.0e-7) + 0x1p-24);
 }
 
-// K5: one warp per lattice
-static __global__ void k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
+// K5: one CTA of two warps per lattice.  Warp 0 reduces the accumulator
+// slots and derives the record and the PCC step; warp 1 meanwhile draws the
+// axis of the next sweep, so the two FP64 chains run on two schedulers at
+// once.  The slot sums are transposed through shared memory so that lane k
+// of warp 0 holds the sum of entry k: one FP64 instruction then converts
+// (and one scales) all of them, instead of a serial chain on one lane.
+constexpr int kFinalizeThreads = 64;
+
+static __global__ void __launch_bounds__(kFinalizeThreads)
+    k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
   const uint32_t rep = blockIdx.x;
   if (rep >= nrep) return;
   const LatDesc &d = descs[rep];
   DevState *st = d.st;
-  const int lane = threadIdx.x;
-  long long v[14], nf = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ long long part[32][kAccStride + 1];
+  __shared__ Axis next;
+  __shared__ double next_beta;
+  static_assert(kSlots == 64 && kAccStride <= 32, "two slots per lane, one entry per lane");
+  if (warp == 1) {
+    if (lane == 0) next = draw_axis(st->quant, st->t + 1u, d.key0, d.key1, d.L);
+  } else {
+    long long *a0 = d.acc + lane * kAccStride, *a1 = d.acc + (lane + 32) * kAccStride;
 #pragma unroll
-  for (int k = 0; k < 14; ++k) v[k] = 0;
-  for (int s = lane; s < kSlots; s += 32) {
-#pragma unroll
-    for (int k = 0; k < 14; ++k) {
-      v[k] += d.acc[s * kAccStride + k];
-      d.acc[s * kAccStride + k] = 0;
+    for (int k = 0; k < kAccStride; ++k) {
+      part[lane][k] = a0[k] + a1[k];
+      a0[k] = 0;
+      a1[k] = 0;
     }
-    nf += d.acc[s * kAccStride + kFlipSlot];
-    d.acc[s * kAccStride + kFlipSlot] = 0;
-  }
-#pragma unroll
-  for (int k = 0; k < 14; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-      v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) nf += __shfl_down_sync(0xFFFFFFFFu, nf, off);
-  if (lane != 0) return;
-  const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
-  double S[14];
-#pragma unroll
-  for (int k = 0; k < 14; ++k) S[k] = static_cast<double>(v[k]) / kFixScale;
-  const double beta = st->beta;
-  ObsRecord o;
-  o.mx = S[0] / n;
-  o.my = S[1] / n;
-  o.m2 = o.mx * o.mx + o.my * o.my;
-  o.ex = S[2] / n;
-  o.sx = S[3] / n;
-  o.ey = S[4] / n;
-  o.sy = S[5] / n;
-  o.energy_per_site = -(S[2] + S[4]) / n;
-  o.upsilon = o.ex - beta * n * o.sx * o.sx;  // Eq. (4), J = 1, T = 1/beta
-  o.beta = beta;
-  o.sweep = st->t;
-  double f2 = 0.0;
-#pragma unroll
-  for (int k = 6; k < 14; ++k) f2 += S[k] * S[k];
-  o.chik = f2 / (2.0 * n);  // 0 unless the lattice measures xi
-  o.flipped = static_cast<uint64_t>(nf);
-  d.rec[st->rec_count % d.rec_cap] = o;
-  st->rec_count += 1;
-  double nb = beta;
-  if (st->pcc_on) {
-    st->pcc_acc += beta * o.upsilon;
-    st->pcc_count += 1;
-    if (st->pcc_count >= st->pcc_block) {
-      const double mean = st->pcc_acc / static_cast<double>(st->pcc_block);
-      double db = st->pcc_dbeta0;
-      if (st->pcc_halve) db = ldexp(db, -static_cast<int>(st->pcc_k / st->pcc_halve));
-      nb = (mean < st->pcc_target) ? beta + db : beta - db;
-      st->pcc_acc = 0.0;
-      st->pcc_count = 0;
+    __syncwarp();
+    long long tot = 0;  // lane k < kAccStride: entry k summed over all slots
+    if (lane < kAccStride) {
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) tot += part[r][lane];
     }
-    st->pcc_k += 1;
+    const double x = static_cast<double>(tot) * (1.0 / kFixScale);  // S_k
+    const double y = x * d.inv_n;                                     // S_k / N
+    double sq = (lane >= 6 && lane < 14) ? x * x : 0.0;  // |F|^2 terms of chik
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, off);
+    const double mx = __shfl_sync(0xFFFFFFFFu, y, 0), my = __shfl_sync(0xFFFFFFFFu, y, 1);
+    const double ex = __shfl_sync(0xFFFFFFFFu, y, 2), sx = __shfl_sync(0xFFFFFFFFu, y, 3);
+    const double ey = __shfl_sync(0xFFFFFFFFu, y, 4), sy = __shfl_sync(0xFFFFFFFFu, y, 5);
+    const double x2 = __shfl_sync(0xFFFFFFFFu, x, 2), x4 = __shfl_sync(0xFFFFFFFFu, x, 4);
+    const long long nf = __shfl_sync(0xFFFFFFFFu, tot, kFlipSlot);
+    if (lane == 0) {
+      const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
+      const double beta = st->beta;
+      ObsRecord o;
+      o.mx = mx;
+      o.my = my;
+      o.m2 = mx * mx + my * my;
+      o.ex = ex;
+      o.sx = sx;
+      o.ey = ey;
+      o.sy = sy;
+      o.energy_per_site = -(x2 + x4) * d.inv_n;
+      o.upsilon = ex - beta * n * sx * sx;  // Eq. (4), J = 1, T = 1/beta
+      o.beta = beta;
+      o.sweep = st->t;
+      o.chik = sq * (0.5 * d.inv_n);  // 0 unless the lattice measures xi
+      o.flipped = static_cast<uint64_t>(nf);
+      d.rec[st->rec_count % d.rec_cap] = o;
+      st->rec_count += 1;
+      double nb = beta;
+      if (st->pcc_on) {
+        st->pcc_acc += beta * o.upsilon;
+        st->pcc_count += 1;
+        if (st->pcc_count >= st->pcc_block) {
+          const double mean = st->pcc_acc / static_cast<double>(st->pcc_block);
+          double db = st->pcc_dbeta0;
+          if (st->pcc_halve) db = ldexp(db, -static_cast<int>(st->pcc_k / st->pcc_halve));
+          nb = (mean < st->pcc_target) ? beta + db : beta - db;
+          st->pcc_acc = 0.0;
+          st->pcc_count = 0;
+        }
+        st->pcc_k += 1;
+      }
+      next_beta = nb;
+    }
   }
-  st->cur ^= 1u;
-  set_sweep_params(st, st->t + 1u, nb, d.key0, d.key1, d.L);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->cur ^= 1u;
+    set_sweep_params(st, st->t + 1u, next_beta, next);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1105,7 +1140,7 @@ static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   st->n_fp64 = 0;
   st->n_fp32_wrong = 0;
   st->err = 0;
-  set_sweep_params(st, 0u, beta, d.key0, d.key1, d.L);
+  set_sweep_params(st, 0u, beta, draw_axis(quant, 0u, d.key0, d.key1, d.L));
 }
 
 static __global__ void k_set_pcc(DevState *st, uint32_t on, double target,

@@ -106,7 +106,7 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
     k_flip_measure<TY, AT, false, false>
         <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
   if ((e = mark(h)) != cudaSuccess) return e;
-  k_finalize<<<1, 32, 0, s>>>(h->d_desc, 1);
+  k_finalize<<<1, kFinalizeThreads, 0, s>>>(h->d_desc, 1);
   if ((e = mark(h)) != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -68,7 +68,7 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
     k_flip_measure<TY, AT, false, true><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   else
     k_flip_measure<TY, AT, false, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
-  k_finalize<<<nrep, 32, 0, s>>>(descs, nrep);
+  k_finalize<<<nrep, kFinalizeThreads, 0, s>>>(descs, nrep);
 }
 
 template <typename AT, bool EXACT>

@@ -132,6 +132,7 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   LatDesc d{};
   d.L = L;
   d.Lmagic = ~0ull / L + 1ull;
+  d.inv_n = 1.0 / (static_cast<double>(L) * L);
   d.ntx = (L + 31) / 32;
   d.nty = (L + kStaticTile - 1) / kStaticTile;
   d.ntiles = d.ntx * d.nty;
