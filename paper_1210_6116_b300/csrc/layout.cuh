@@ -32,7 +32,7 @@ struct Layout {
   uint32_t L, TY, ntx, nty, ntiles, rec_cap;
   size_t esize;
   size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0,
-      off_theta1, off_label, off_rplane, off_dplane, off_coin, off_wave, total;
+      off_theta1, off_label, off_rplane, off_dplane, off_edge, off_coin, off_wave, total;
 };
 
 inline xy_status make_layout(const xy_config *c, Layout *lo) {
@@ -75,6 +75,7 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
   lo->off_label = take(n * sizeof(uint32_t));
   lo->off_rplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
   lo->off_dplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
+  lo->off_edge = take(static_cast<size_t>(lo->ntiles) * (2 * ty + 64) * sizeof(uint32_t));
   lo->off_coin = take((n / 32 + 2) * sizeof(uint32_t));
   lo->off_wave = take(static_cast<size_t>(c->L) * 8);
   lo->total = off;
@@ -100,6 +101,7 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.label = reinterpret_cast<uint32_t *>(ws + lo.off_label);
   d.rplane = reinterpret_cast<uint32_t *>(ws + lo.off_rplane);
   d.dplane = reinterpret_cast<uint32_t *>(ws + lo.off_dplane);
+  d.edge = reinterpret_cast<uint32_t *>(ws + lo.off_edge);
   d.coin = reinterpret_cast<uint32_t *>(ws + lo.off_coin);
   d.xi = cfg->measure_xi ? 1u : 0u;
   d.wolff = cfg->update == XY_UPDATE_WOLFF ? 1u : 0u;

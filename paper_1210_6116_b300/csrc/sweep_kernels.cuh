@@ -95,6 +95,7 @@ struct LatDesc {
   void *theta[2];
   uint32_t *label;
   uint32_t *rplane, *dplane;
+  uint32_t *edge;  // per tile: labels of its left/right columns, top/bottom rows
   uint32_t *coin;
   long long *acc;
   DevState *st;
@@ -359,6 +360,15 @@ __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
 // ---------------------------------------------------------------------------
 constexpr uint32_t kNoRoot = 0xFFFFFFFFu;
 
+// Edge table of a 32 x TY tile, written by K1 and read by the merge: the
+// tile-local root (a global site index) of every site on its boundary, as
+// [left column: TY][right column: TY][top row: 32][bottom row: 32].  The
+// merge reads these compactly instead of one sector per label of a column.
+template <int TY>
+__host__ __device__ constexpr uint32_t edge_words() {
+  return 2u * TY + 64u;
+}
+
 // lanes of the run containing `lane`: [start, end]
 __device__ __forceinline__ uint32_t run_start_of(uint32_t starts, int lane) {
   return 31u - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
@@ -604,15 +614,21 @@ __global__ void __launch_bounds__(kThreads, 4)
                r0 * 32u + run_start_of(~(Rb << 1), lane));
     }
     __syncthreads();
-    // every site: root of its run's root as recorded by the scan
+    // every site: root of its run's root as recorded by the scan; boundary
+    // sites also into the tile's edge table
+    uint32_t *edge = d.edge + static_cast<uint64_t>(tile) * edge_words<TY>();
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       if (static_cast<uint32_t>(k) >= nb) break;
       const uint32_t r = r0 + k;
       if (col_ok) {
         const uint32_t root = sfind(par, labs[k]);
-        d.label[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] =
-            (g.y0 + (root >> 5)) * L + g.x0 + (root & 31u);
+        const uint32_t v = (g.y0 + (root >> 5)) * L + g.x0 + (root & 31u);
+        d.label[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] = v;
+        if (lane == 0) edge[r] = v;                                      // left column
+        if (static_cast<uint32_t>(lane) + 1u == g.w) edge[TY + r] = v;  // right column
+        if (r == 0u) edge[2 * TY + lane] = v;                           // top row
+        if (r + 1u == g.h) edge[2 * TY + 32 + lane] = v;                // bottom row
       }
     }
     __syncthreads();
@@ -626,10 +642,13 @@ __global__ void __launch_bounds__(kThreads, 4)
 // An edge bond is skipped when the previous edge of the same side is active
 // and both pairs of endpoints are joined by a direct bond along the edge: the
 // previous edge then unites the same two clusters.
+// On an active edge bond, *ea and *eb are the edge-table entries of its two
+// endpoints.
 template <int TY>
 __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
-                                          uint32_t j, uint32_t *a,
-                                          uint32_t *b) {
+                                          uint32_t j, uint64_t *ea,
+                                          uint64_t *eb) {
+  constexpr uint32_t EW = edge_words<TY>();
   const uint32_t L = d.L;
   const Tile g = tile_geom<TY>(L, d.ntx, tile);
   const uint64_t base = static_cast<uint64_t>(tile) * TY;
@@ -637,31 +656,30 @@ __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
     if (j >= g.h) return false;
     const uint32_t bit = g.w - 1u;
     if (!((__ldg(d.rplane + base + j) >> bit) & 1u)) return false;
+    // the neighbouring tile to the right holds column xh as its column 0
+    const uint32_t tx = tile % d.ntx;
+    const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
     if (j > 0 && ((__ldg(d.rplane + base + j - 1) >> bit) & 1u) &&
         ((__ldg(d.dplane + base + j - 1) >> bit) & 1u)) {
-      // the neighbouring tile to the right holds column xh at bit 0
-      const uint32_t tx = tile % d.ntx;
-      const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
       if (__ldg(d.dplane + static_cast<uint64_t>(tn) * TY + j - 1) & 1u) return false;
     }
-    const uint32_t y = g.y0 + j;
-    *a = y * L + g.x0 + g.w - 1u;
-    *b = y * L + g.xh;
+    *ea = static_cast<uint64_t>(tile) * EW + TY + j;  // right column, row j
+    *eb = static_cast<uint64_t>(tn) * EW + j;         // its left column, row j
     return true;
   }
   const uint32_t c = j - TY;
   if (c >= g.w) return false;
   const uint32_t D = __ldg(d.dplane + base + g.h - 1u);
   if (!((D >> c) & 1u)) return false;
+  // the tile below holds row yh as its row 0, same columns
+  const uint32_t ty = tile / d.ntx;
+  const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tile % d.ntx;
   if (c > 0 && ((D >> (c - 1u)) & 1u) &&
       ((__ldg(d.rplane + base + g.h - 1u) >> (c - 1u)) & 1u)) {
-    // the tile below holds row yh as its row 0, same columns
-    const uint32_t ty = tile / d.ntx;
-    const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tile % d.ntx;
     if ((__ldg(d.rplane + static_cast<uint64_t>(tb) * TY) >> (c - 1u)) & 1u) return false;
   }
-  *a = (g.y0 + g.h - 1u) * L + g.x0 + c;
-  *b = g.yh * L + g.x0 + c;
+  *ea = static_cast<uint64_t>(tile) * EW + 2 * TY + 32 + c;  // bottom row, column c
+  *eb = static_cast<uint64_t>(tb) * EW + 2 * TY + c;         // its top row, column c
   return true;
 }
 
@@ -678,11 +696,12 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t rep = find_rep(prefix, nrep, work);
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
-  uint32_t a, b;
-  // start from the tile roots: labels of non-root sites are never written
-  // here, so after the merge every site still points at its tile root
-  if (edge_bond<TY>(d, tile, j, &a, &b))
-    gunion(d.label, __ldcg(d.label + a), __ldcg(d.label + b), d.st);
+  uint64_t ea, eb;
+  // start from the tile roots (from the edge table): labels of non-root sites
+  // are never written here, so after the merge every site still points at
+  // its tile root
+  if (edge_bond<TY>(d, tile, j, &ea, &eb))
+    gunion(d.label, __ldg(d.edge + ea), __ldg(d.edge + eb), d.st);
 }
 
 // K3: after all unions, every merged tile root re-points at its grandparent
@@ -700,14 +719,6 @@ __device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st) {
   atomicOr(&st->err, kErrFindCap);
 }
 
-__device__ __forceinline__ void compress(uint32_t *lab, uint32_t a,
-                                         DevState *st) {
-  // a is an edge site: jump its tile root (its label, unless a is itself a
-  // tile root whose entry the merge already moved) and a itself
-  const uint32_t t = __ldcg(lab + a);
-  jump(lab, t, st);
-  jump(lab, a, st);
-}
 
 template <int TY>
 __global__ void __launch_bounds__(kThreads)
@@ -722,10 +733,13 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t rep = find_rep(prefix, nrep, work);
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
-  uint32_t a, b;
-  if (edge_bond<TY>(d, tile, j, &a, &b)) {
-    compress(d.label, a, d.st);
-    compress(d.label, b, d.st);
+  // the tile roots of both endpoints: every entry the merge changed belongs
+  // to such a root (finds and links start from them and only reach their
+  // ancestors, which are such roots too)
+  uint64_t ea, eb;
+  if (edge_bond<TY>(d, tile, j, &ea, &eb)) {
+    jump(d.label, __ldg(d.edge + ea), d.st);
+    jump(d.label, __ldg(d.edge + eb), d.st);
   }
 }
 
@@ -747,7 +761,8 @@ constexpr size_t flip_smem() {
 // column) and also resolves the row below its band (the next band's first
 // row, or the row below the tile) and, with lanes 0..B-1, the column right of
 // the tile.  Roots come in two batched rounds of loads: a site's entry (its
-// tile root, or its root when k_compress jumped it), then that entry's entry,
+// tile root, or its root where this kernel already rewrote it), then that
+// entry's entry,
 // which k_compress has made the root (every merged tile root is jumped until
 // its parent is a root; an unmerged one is its own entry).
 // EXT: the extended instantiation, for lattice tables where some lattice
