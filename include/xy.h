@@ -207,6 +207,15 @@ xy_status xy_get_bonds(xy_lattice *h, uint8_t *host_right,
 /* Cluster labels of the last sweep: N uint32, label = minimum site index of
  * the cluster. */
 xy_status xy_get_labels(xy_lattice *h, uint32_t *host_dst);
+/* Sampled state of the last sweep, for checks at sizes whose full arrays are
+ * too large to copy: for each of the n site indices in host_sites (each
+ * < N; XY_EINVAL otherwise) the stored angle (lattice dtype: float, or the
+ * 16 bits of an FP16 or u16 angle), the label, and the bonds as
+ * bit 0 = right, bit 1 = down.  Any of the three outputs may be NULL.
+ * Synchronising; allocates a device buffer of about 17 n bytes for the call
+ * and frees it before returning (a diagnostic, not for the sweep loop). */
+xy_status xy_get_sites(xy_lattice *h, const uint64_t *host_sites, uint32_t n,
+                       void *host_theta, uint32_t *host_label, uint8_t *host_bonds);
 /* Label caller-supplied bond bytes (N each, same meaning as xy_get_bonds)
  * with the device labeling kernels; writes N labels.  Does not touch the
  * angles, the sweep counter or the records. */

@@ -51,7 +51,8 @@ STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "X
 EXPORTS = (
     "xy_last_error", "xy_workspace_size", "xy_init", "xy_sweep", "xy_pcc_step",
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
-    "xy_get_bonds", "xy_get_labels", "xy_label_bonds", "xy_get_band_stats", "xy_save",
+    "xy_get_bonds", "xy_get_labels", "xy_get_sites", "xy_label_bonds", "xy_get_band_stats",
+    "xy_save",
     "xy_load", "xy_run_host", "xy_profile", "xy_profile_read", "xy_label_bonds_static",
     "xy_engine_workspace_size", "xy_engine_create", "xy_engine_admit", "xy_engine_retire",
     "xy_engine_step", "xy_engine_measure", "xy_engine_get_angles", "xy_engine_get_state",
@@ -123,6 +124,7 @@ def load_library() -> ctypes.CDLL:
         "xy_set_angles": (I, [P, P]),
         "xy_get_bonds": (I, [P, P, P]),
         "xy_get_labels": (I, [P, P]),
+        "xy_get_sites": (I, [P, P, ctypes.c_uint32, P, P, P]),
         "xy_label_bonds": (I, [P, P, P, P]),
         "xy_get_band_stats": (I, [P, P, P]),
         "xy_save": (I, [P, P, P]),
@@ -288,6 +290,17 @@ class Lattice:
         out = np.zeros(self.n, np.uint32)
         _check(load_library().xy_get_labels(self.handle, _ptr(out)))
         return out
+
+    def get_sites(self, sites):
+        """(angles, labels, bonds) of the listed sites after the last sweep;
+        bonds: bit 0 right, bit 1 down."""
+        sites = np.ascontiguousarray(sites, dtype=np.uint64)
+        th = np.zeros(sites.size, self.np_dtype)
+        lab = np.zeros(sites.size, np.uint32)
+        bd = np.zeros(sites.size, np.uint8)
+        _check(load_library().xy_get_sites(self.handle, _ptr(sites), sites.size, _ptr(th),
+                                           _ptr(lab), _ptr(bd)))
+        return th, lab, bd
 
     def label_bonds(self, right: np.ndarray, down: np.ndarray) -> np.ndarray:
         r = np.ascontiguousarray(right, np.uint8)

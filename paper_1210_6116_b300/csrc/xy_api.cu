@@ -207,6 +207,24 @@ xy_status check_device_error(xy_lattice *h) {
 
 }  // namespace
 
+// Sampled state for xy_get_sites: angle (raw bits of the storage format),
+// label and the two bond bits of each listed site.  16-bit formats (FP16 and
+// u16) are copied as their bits.
+template <typename AT>
+__global__ void k_gather_sites(LatDesc d, uint32_t TY, const uint64_t *__restrict__ sites,
+                               uint32_t n, uint32_t cur, AT *theta_out, uint32_t *label_out,
+                               uint8_t *bonds_out) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint64_t i = sites[k];
+  const uint32_t x = static_cast<uint32_t>(i % d.L), y = static_cast<uint32_t>(i / d.L);
+  theta_out[k] = static_cast<const AT *>(d.theta[cur])[i];
+  label_out[k] = d.label[i];
+  const uint64_t w = static_cast<uint64_t>((y / TY) * d.ntx + x / 32u) * TY + y % TY;
+  bonds_out[k] = static_cast<uint8_t>(((d.rplane[w] >> (x & 31u)) & 1u) |
+                                      (((d.dplane[w] >> (x & 31u)) & 1u) << 1));
+}
+
 extern "C" {
 
 const char *xy_last_error(void) { return g_err; }
@@ -471,6 +489,45 @@ xy_status xy_get_labels(xy_lattice *h, uint32_t *host_dst) {
   XY_CUDA(cudaStreamSynchronize(h->stream));
   XY_CUDA(cudaMemcpy(host_dst, h->desc.label, static_cast<size_t>(h->lo.L) * h->lo.L * 4,
                      cudaMemcpyDeviceToHost));
+  return XY_OK;
+}
+
+xy_status xy_get_sites(xy_lattice *h, const uint64_t *host_sites, uint32_t n,
+                       void *host_theta, uint32_t *host_label, uint8_t *host_bonds) {
+  if (!h || (n > 0 && !host_sites)) return fail(XY_EINVAL, "NULL argument");
+  if (n == 0) return XY_OK;
+  const uint64_t N = static_cast<uint64_t>(h->lo.L) * h->lo.L;
+  for (uint32_t k = 0; k < n; ++k)
+    if (host_sites[k] >= N)
+      return fail(XY_EINVAL, "site %llu outside 0..N-1", static_cast<unsigned long long>(host_sites[k]));
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  DevState st;
+  XY_CUDA(cudaMemcpy(&st, h->d_state, sizeof(st), cudaMemcpyDeviceToHost));
+  const size_t es = h->lo.esize;
+  const size_t off_t = static_cast<size_t>(n) * 8, off_l = off_t + align_up(n * es, 16),
+               off_b = off_l + static_cast<size_t>(n) * 4, bytes = off_b + n;
+  char *buf = nullptr;
+  XY_CUDA(cudaMalloc(&buf, bytes));
+  cudaError_t e = cudaMemcpy(buf, host_sites, static_cast<size_t>(n) * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const uint64_t *sites = reinterpret_cast<const uint64_t *>(buf);
+    uint32_t *lab = reinterpret_cast<uint32_t *>(buf + off_l);
+    uint8_t *bd = reinterpret_cast<uint8_t *>(buf + off_b);
+    const uint32_t blocks = (n + 255) / 256;
+    if (h->cfg.angle_dtype == XY_F32)
+      k_gather_sites<float><<<blocks, 256>>>(h->desc, h->lo.TY, sites, n, st.cur,
+                                             reinterpret_cast<float *>(buf + off_t), lab, bd);
+    else
+      k_gather_sites<uint16_t><<<blocks, 256>>>(h->desc, h->lo.TY, sites, n, st.cur,
+                                                reinterpret_cast<uint16_t *>(buf + off_t), lab, bd);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && host_theta) e = cudaMemcpy(host_theta, buf + off_t, n * es, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_label) e = cudaMemcpy(host_label, lab, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_bonds) e = cudaMemcpy(host_bonds, bd, n, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(XY_ECUDA, "xy_get_sites: %s", cudaGetErrorString(e));
   return XY_OK;
 }
 

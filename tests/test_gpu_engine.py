@@ -111,3 +111,24 @@ def test_engine_rejects_bad_lattices():
     with pytest.raises(xy.XyError) as e:
         eng.admit(eng.config(64, 1.0, 2))   # no free slot
     assert e.value.status == xy.XY_ENOMEM
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_full_batch_sampled_replicas_equal_alone(dtype):
+    """The batched workload at full size (256 replicas, L from {64 .. 2048},
+    beta in [1.0, 1.3], FP32 thresholds, tile 32 x 64): after 3 sweeps,
+    sampled replicas of every size equal their alone runs bit for bit."""
+    table = synth.replica_table(256, seed=3, sizes=(64, 128, 256, 512, 1024, 2048),
+                                beta_range=(1.0, 1.3))
+    eng = xy.Engine(len(table), dtype=dtype, exact=False, tile_y=64)
+    slots = [eng.admit(eng.config(r["L"], r["beta"], r["seed"])) for r in table]
+    eng.step(3)
+    picked = {}
+    for k, r in enumerate(table):
+        picked.setdefault(r["L"], k)
+    for L, k in sorted(picked.items()):
+        r = table[k]
+        recs, ang = _alone(r["L"], r["beta"], r["seed"], 3, dtype=dtype, tile_y=64)
+        np.testing.assert_array_equal(eng.measure(slots[k]), recs)
+        np.testing.assert_array_equal(eng.get_angles(slots[k]).view(np.uint8), ang.view(np.uint8))
+    eng.close()
