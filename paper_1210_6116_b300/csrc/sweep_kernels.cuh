@@ -639,11 +639,10 @@ __global__ void __launch_bounds__(kThreads, 4)
 // K2: merge across tile edges.  Work item = (tile, j): j < TY is the right
 // edge of tile row j, j >= TY the bottom edge of column j - TY.
 // ---------------------------------------------------------------------------
-// An edge bond is skipped when the previous edge of the same side is active
-// and both pairs of endpoints are joined by a direct bond along the edge: the
-// previous edge then unites the same two clusters.
 // On an active edge bond, *ea and *eb are the edge-table entries of its two
-// endpoints.
+// endpoints.  (Repeated unions of the same two tile roots are grouped in
+// k_merge; a check of the neighbouring bonds here saved fewer of them than
+// its plane loads cost.)
 template <int TY>
 __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
                                           uint32_t j, uint64_t *ea,
@@ -659,10 +658,6 @@ __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
     // the neighbouring tile to the right holds column xh as its column 0
     const uint32_t tx = tile % d.ntx;
     const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
-    if (j > 0 && ((__ldg(d.rplane + base + j - 1) >> bit) & 1u) &&
-        ((__ldg(d.dplane + base + j - 1) >> bit) & 1u)) {
-      if (__ldg(d.dplane + static_cast<uint64_t>(tn) * TY + j - 1) & 1u) return false;
-    }
     *ea = static_cast<uint64_t>(tile) * EW + TY + j;  // right column, row j
     *eb = static_cast<uint64_t>(tn) * EW + j;         // its left column, row j
     return true;
@@ -674,10 +669,6 @@ __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
   // the tile below holds row yh as its row 0, same columns
   const uint32_t ty = tile / d.ntx;
   const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tile % d.ntx;
-  if (c > 0 && ((D >> (c - 1u)) & 1u) &&
-      ((__ldg(d.rplane + base + g.h - 1u) >> (c - 1u)) & 1u)) {
-    if ((__ldg(d.rplane + static_cast<uint64_t>(tb) * TY) >> (c - 1u)) & 1u) return false;
-  }
   *ea = static_cast<uint64_t>(tile) * EW + 2 * TY + 32 + c;  // bottom row, column c
   *eb = static_cast<uint64_t>(tb) * EW + 2 * TY + c;         // its top row, column c
   return true;
@@ -796,7 +787,11 @@ constexpr size_t flip_smem() {
 // measures chik (d.xi) or runs Wolff updates (d.wolff); each lattice still
 // takes only what its own flags ask for.  The lean one does neither and
 // keeps its registers (launch bounds 5 CTAs/SM; EXT needs 4).
-template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false>
+// WL: also store the canonical labels (for a sweep whose labels the host may
+// read back, and always with LABELS_ONLY); otherwise the next sweep's K1
+// overwrites them, and leaving the store out saves ~8 us per sweep at
+// L = 4096.
+template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false, bool WL = true>
 __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
@@ -856,10 +851,12 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       if (static_cast<uint32_t>(k) <= nb && col_ok) l[k] = p[k];
     if (vc) lc = pc;
     // canonical labels of the band's own sites
+    if constexpr (LABELS_ONLY || WL) {
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (static_cast<uint32_t>(k) < nb && col_ok)
-        __stcg(lab + static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane, l[k]);
+      for (int k = 0; k < B; ++k) {
+        if (static_cast<uint32_t>(k) < nb && col_ok)
+          __stcg(lab + static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane, l[k]);
+      }
     }
     if (LABELS_ONLY) continue;
     // round 4: which sites reflect.  SW: the coin of the site's root.

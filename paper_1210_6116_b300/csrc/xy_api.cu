@@ -58,6 +58,7 @@ struct xy_lattice {
   uint32_t *d_prefix;
   DevState *d_state;
   uint64_t enqueued;  // sweeps enqueued since xy_init
+  bool write_labels = true;  // the next sweep stores canonical labels
   uint64_t reported;  // sweeps already returned by xy_measure
   int sm_count;
   // kernel timing: 6 events per sweep bracket its 5 kernels
@@ -99,11 +100,20 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   if ((e = mark(h)) != cudaSuccess) return e;
   k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   if ((e = mark(h)) != cudaSuccess) return e;
-  if (h->desc.xi || h->desc.wolff)  // chik sums or Wolff: the extended K4
-    k_flip_measure<TY, AT, false, true>
+  // the extended K4 for chik sums or Wolff; canonical labels only for the
+  // last sweep of an xy_sweep / xy_pcc_step call
+  const bool ext = h->desc.xi || h->desc.wolff;
+  if (ext && h->write_labels)
+    k_flip_measure<TY, AT, false, true, true>
+        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  else if (ext)
+    k_flip_measure<TY, AT, false, true, false>
+        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  else if (h->write_labels)
+    k_flip_measure<TY, AT, false, false, true>
         <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
   else
-    k_flip_measure<TY, AT, false, false>
+    k_flip_measure<TY, AT, false, false, false>
         <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
   if ((e = mark(h)) != cudaSuccess) return e;
   k_finalize<<<1, kFinalizeThreads, 0, s>>>(h->d_desc, 1);
@@ -307,7 +317,10 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
 xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 0u, 0.0, 0.0, 0u, 1u);
-  for (uint32_t k = 0; k < n_sweeps; ++k) XY_CUDA(launch_sweep(h));
+  for (uint32_t k = 0; k < n_sweeps; ++k) {
+    h->write_labels = k + 1 == n_sweeps;  // labels of the call's last sweep
+    XY_CUDA(launch_sweep(h));
+  }
   XY_CUDA(cudaGetLastError());
   h->enqueued += n_sweeps;
   return XY_OK;
@@ -321,7 +334,10 @@ xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p, uint32_t n_sweeps) 
     return fail(XY_EINVAL, "dbeta0 must be finite and >= 0, target finite");
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 1u, p->target, p->dbeta0, p->halve_every,
                                     p->block);
-  for (uint32_t k = 0; k < n_sweeps; ++k) XY_CUDA(launch_sweep(h));
+  for (uint32_t k = 0; k < n_sweeps; ++k) {
+    h->write_labels = k + 1 == n_sweeps;  // labels of the call's last sweep
+    XY_CUDA(launch_sweep(h));
+  }
   XY_CUDA(cudaGetLastError());
   h->enqueued += n_sweeps;
   return XY_OK;

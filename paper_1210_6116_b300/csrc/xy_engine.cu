@@ -64,10 +64,11 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
   k_merge<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
   k_compress<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
+  // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
-    k_flip_measure<TY, AT, false, true><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
+    k_flip_measure<TY, AT, false, true, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   else
-    k_flip_measure<TY, AT, false, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
+    k_flip_measure<TY, AT, false, false, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
   k_finalize<<<nrep, kFinalizeThreads, 0, s>>>(descs, nrep);
 }
 
