@@ -35,13 +35,18 @@ UNIT = "spin updates/ns"
 # Algorithmic bytes per site of each kernel (FP32 angles): what the step must
 # move at minimum for that kernel's share of the work.
 KERNEL_BYTES_PER_SITE = {
-    "bond_label": 4.0 + 4.0 + 0.25 + 0.125,   # angles in, tile labels out, bond planes, coin bits
-    "flip_measure": 4.0 + 4.0 + 4.0 + 4.0,    # labels in/out, angles in/out
+    # angles in, tile labels out, bond planes, coin bits, tile edge table
+    "bond_label": 4.0 + 4.0 + 0.25 + 0.125 + 0.375,
+    # labels in, angles in and out (canonical labels are stored only by the
+    # last sweep of a call)
+    "flip_measure": 4.0 + 4.0 + 4.0,
 }
-# Whole-sweep byte models (per site): the method's minimum with canonical
-# labels materialised, and the pipeline this library runs.
-M_CANON = 16.5
-M_BUILT = 4.0 + 4.0 + 0.375 + 16.0
+# Whole-sweep byte models (per site): the method's minimum (angles read and
+# written once, one label per site written once and read once, bond and
+# coin bits), and the pipeline this library runs (K1, merge and compress
+# at ~0.5 B/site each, K4).
+M_CANON = 4.0 + 4.0 + 4.0 + 4.0 + 0.375
+M_BUILT = KERNEL_BYTES_PER_SITE["bond_label"] + 0.5 + 0.5 + KERNEL_BYTES_PER_SITE["flip_measure"]
 
 
 def _sm_max_mhz():
