@@ -1024,7 +1024,8 @@ __device__ inline Axis draw_axis(uint32_t quant, uint32_t t, uint32_t k0, uint32
   return a;
 }
 
-__device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta, const Axis &a) {
+__device__ inline void set_sweep_params(DevState *st, uint32_t quant, uint32_t t, double beta,
+                                        const Axis &a) {
   st->t = t;
   st->beta = beta;
   st->cphi = a.c;
@@ -1036,7 +1037,7 @@ __device__ inline void set_sweep_params(DevState *st, uint32_t t, double beta, c
   st->beta2_32 = __double2float_rn(2.0 * beta);
   // band half-width: 4x the error bound of the FP32 evaluation of u - p;
   // u16 adds <= 4.2e-7 per projection for the FP32 angle q 2pi_f 2^-16
-  const double dx = st->quant ? 3.0e-6 : 2.0e-6;
+  const double dx = quant ? 3.0e-6 : 2.0e-6;
   st->eps = __double2float_rn(4.0 * (2.0 * beta * dx + 3.0e-7) + 0x1p-24);
 }
 
@@ -1052,15 +1053,20 @@ static __global__ void __launch_bounds__(kFinalizeThreads)
     k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
   const uint32_t rep = blockIdx.x;
   if (rep >= nrep) return;
-  const LatDesc &d = descs[rep];
+  // The kernel is a chain of dependent memory accesses (ncu: ~11 us for
+  // under a thousand instructions when each field was loaded where it was
+  // used), so everything it reads is loaded in one batch: the descriptor and
+  // the state as whole structs, then the accumulator slots beside the state.
+  const LatDesc d = descs[rep];
   DevState *st = d.st;
+  const DevState s0 = *st;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ long long part[32][kAccStride + 1];
   __shared__ Axis next;
-  __shared__ double next_beta;
   static_assert(kSlots == 64 && kAccStride <= 32, "two slots per lane, one entry per lane");
+  double nb = s0.beta;  // beta of the next sweep (thread 0)
   if (warp == 1) {
-    if (lane == 0) next = draw_axis(st->quant, st->t + 1u, d.key0, d.key1, d.L);
+    if (lane == 0) next = draw_axis(s0.quant, s0.t + 1u, d.key0, d.key1, d.L);
   } else {
     long long *a0 = d.acc + lane * kAccStride, *a1 = d.acc + (lane + 32) * kAccStride;
 #pragma unroll
@@ -1087,7 +1093,7 @@ static __global__ void __launch_bounds__(kFinalizeThreads)
     const long long nf = __shfl_sync(0xFFFFFFFFu, tot, kFlipSlot);
     if (lane == 0) {
       const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
-      const double beta = st->beta;
+      const double beta = s0.beta;
       ObsRecord o;
       o.mx = mx;
       o.my = my;
@@ -1099,32 +1105,32 @@ static __global__ void __launch_bounds__(kFinalizeThreads)
       o.energy_per_site = -(x2 + x4) * d.inv_n;
       o.upsilon = ex - beta * n * sx * sx;  // Eq. (4), J = 1, T = 1/beta
       o.beta = beta;
-      o.sweep = st->t;
+      o.sweep = s0.t;
       o.chik = sq * (0.5 * d.inv_n);  // 0 unless the lattice measures xi
       o.flipped = static_cast<uint64_t>(nf);
-      d.rec[st->rec_count % d.rec_cap] = o;
-      st->rec_count += 1;
-      double nb = beta;
-      if (st->pcc_on) {
-        st->pcc_acc += beta * o.upsilon;
-        st->pcc_count += 1;
-        if (st->pcc_count >= st->pcc_block) {
-          const double mean = st->pcc_acc / static_cast<double>(st->pcc_block);
-          double db = st->pcc_dbeta0;
-          if (st->pcc_halve) db = ldexp(db, -static_cast<int>(st->pcc_k / st->pcc_halve));
-          nb = (mean < st->pcc_target) ? beta + db : beta - db;
-          st->pcc_acc = 0.0;
-          st->pcc_count = 0;
+      d.rec[s0.rec_count % d.rec_cap] = o;
+      st->rec_count = s0.rec_count + 1;
+      if (s0.pcc_on) {
+        double acc = s0.pcc_acc + beta * o.upsilon;
+        uint32_t count = s0.pcc_count + 1;
+        if (count >= s0.pcc_block) {
+          const double mean = acc / static_cast<double>(s0.pcc_block);
+          double db = s0.pcc_dbeta0;
+          if (s0.pcc_halve) db = ldexp(db, -static_cast<int>(s0.pcc_k / s0.pcc_halve));
+          nb = (mean < s0.pcc_target) ? beta + db : beta - db;
+          acc = 0.0;
+          count = 0;
         }
-        st->pcc_k += 1;
+        st->pcc_acc = acc;
+        st->pcc_count = count;
+        st->pcc_k = s0.pcc_k + 1;
       }
-      next_beta = nb;
     }
   }
-  __syncthreads();
+  __syncthreads();  // both warps: the next axis from warp 1
   if (threadIdx.x == 0) {
-    st->cur ^= 1u;
-    set_sweep_params(st, st->t + 1u, next_beta, next);
+    st->cur = s0.cur ^ 1u;
+    set_sweep_params(st, s0.quant, s0.t + 1u, nb, next);
   }
 }
 
@@ -1179,7 +1185,7 @@ static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   st->n_fp64 = 0;
   st->n_fp32_wrong = 0;
   st->err = 0;
-  set_sweep_params(st, 0u, beta, draw_axis(quant, 0u, d.key0, d.key1, d.L));
+  set_sweep_params(st, quant, 0u, beta, draw_axis(quant, 0u, d.key0, d.key1, d.L));
 }
 
 static __global__ void k_set_pcc(DevState *st, uint32_t on, double target,
