@@ -34,6 +34,7 @@ UNIT = "spin updates/ns"
 
 # Algorithmic bytes per site of each kernel (FP32 angles): what the step must
 # move at minimum for that kernel's share of the work.
+PROFILE_EVERY = 16  # kernel-timing stride inside timed regions
 KERNEL_BYTES_PER_SITE = {
     # angles in, tile labels out, bond planes, coin bits, tile edge table
     "bond_label": 4.0 + 4.0 + 0.25 + 0.125 + 0.375,
@@ -163,7 +164,10 @@ def run_ours(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    lat.profile(True)
+    # kernel durations from every 16th sweep of the timed region: the events
+    # bracketing a sweep's kernels cost it ~12 us, so timing every sweep
+    # would understate the rate by ~4 %
+    lat.profile(True, every=PROFILE_EVERY)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         done = 0
@@ -233,6 +237,7 @@ def run_ours(args):
                                "frac_canon": round(value * M_CANON / peak, 4),
                                "frac_built": round(value * M_BUILT / peak, 4)},
             "kernels": kernels,
+            "kernel_timing": f"CUDA events around the kernels of every {PROFILE_EVERY}th sweep of the timed region",
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "last_energy_per_site": float(recs[-1]["energy_per_site"]) if len(recs) else None,
@@ -318,7 +323,7 @@ def storage_report(xy, L, beta, args):
         lat = xy.Lattice(L, beta, seed=4343, tile_y=args.tile_y, exact=bool(args.exact), dtype=dt)
         lat.sweep(5)
         torch.cuda.synchronize()
-        lat.profile(True)
+        lat.profile(True, every=PROFILE_EVERY)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(lat.stream)

@@ -249,8 +249,10 @@ typedef struct {
   double ms[XY_NUM_KERNELS];          /* summed device time (CUDA events)  */
   uint64_t launches[XY_NUM_KERNELS];  /* launches timed                    */
 } xy_kernel_times;
-/* enable = 1: from now on bracket every kernel of every sweep with CUDA
- * events on the lattice's stream (resets the totals); enable = 0: stop. */
+/* enable = k >= 1: from now on bracket every kernel of every k-th sweep
+ * with CUDA events on the lattice's stream (resets the totals; the events
+ * cost the sweep a few us each, so a stride keeps a timed run honest);
+ * enable = 0: stop.  XY_EINVAL for enable < 0. */
 xy_status xy_profile(xy_lattice *h, int enable);
 /* Synchronise and return the totals since profiling was enabled. */
 xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out);

@@ -321,8 +321,10 @@ class Lattice:
         _check(load_library().xy_run_host(self.handle, pin(angles_in), n_sweeps,
                                           pin(obs_out), pin(angles_out)))
 
-    def profile(self, enable: bool):
-        _check(load_library().xy_profile(self.handle, 1 if enable else 0))
+    def profile(self, enable: bool, every: int = 1):
+        """Time the kernels of every `every`-th sweep with CUDA events (the
+        events slow the timed sweeps by a few us each)."""
+        _check(load_library().xy_profile(self.handle, int(every) if enable else 0))
 
     def profile_read(self) -> dict:
         t = xy_kernel_times()

@@ -62,7 +62,9 @@ struct xy_lattice {
   uint64_t reported;  // sweeps already returned by xy_measure
   int sm_count;
   // kernel timing: 6 events per sweep bracket its 5 kernels
-  bool prof;
+  uint32_t prof;       // 0: off; k: time every k-th sweep
+  uint64_t prof_count;  // sweeps launched since profiling was enabled
+  bool prof_this;       // the sweep being launched is timed
   std::vector<cudaEvent_t> events;
   size_t ev_used;
 };
@@ -71,7 +73,7 @@ namespace {
 
 // records the next timing event of a profiled sweep (no-op otherwise)
 cudaError_t mark(xy_lattice *h) {
-  if (!h->prof) return cudaSuccess;
+  if (!h->prof_this) return cudaSuccess;
   if (h->ev_used == h->events.size()) {
     cudaEvent_t e;
     cudaError_t err = cudaEventCreate(&e);
@@ -83,6 +85,7 @@ cudaError_t mark(xy_lattice *h) {
 
 template <int TY, typename AT, bool EXACT>
 cudaError_t launch_sweep_t(xy_lattice *h) {
+  h->prof_this = h->prof != 0 && h->prof_count++ % h->prof == 0;
   const uint32_t nw = h->lo.ntiles;
   cudaStream_t s = h->stream;
   cudaError_t e;
@@ -422,7 +425,9 @@ xy_status xy_run_host(xy_lattice *h, const void *host_angles_in, uint32_t n_swee
 xy_status xy_profile(xy_lattice *h, int enable) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
   XY_CUDA(cudaStreamSynchronize(h->stream));
-  h->prof = enable != 0;
+  if (enable < 0) return fail(XY_EINVAL, "enable must be >= 0");
+  h->prof = static_cast<uint32_t>(enable);
+  h->prof_count = 0;
   h->ev_used = 0;
   return XY_OK;
 }
