@@ -305,7 +305,7 @@ xy_status xy_engine_destroy(xy_engine *e);
  * active, same meaning as xy_get_bonds) of an L x L periodic lattice into
  * d_labels (device array of L*L uint32: minimum site index of each cluster),
  * with the same kernels as xy_label_bonds.  Its scratch is a fixed array
- * built into the library (about 0.79 MB on every GPU that loads it, kept
+ * built into the library (about 1.05 MB on every GPU that loads it, kept
  * until the process exits); it calls no cudaMalloc/cudaFree.
  *   - L is limited to 2..XY_STATIC_MAX_L; larger L returns XY_EINVAL.
  *   - The first call on a device looks up the scratch's device address

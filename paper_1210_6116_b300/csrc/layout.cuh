@@ -32,7 +32,8 @@ struct Layout {
   uint32_t L, TY, ntx, nty, ntiles, rec_cap;
   size_t esize;
   size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0,
-      off_theta1, off_label, off_rplane, off_dplane, off_edge, off_coin, off_wave, total;
+      off_theta1, off_label, off_rplane, off_dplane, off_edge, off_links, off_link_count, off_coin,
+      off_wave, total;
 };
 
 inline xy_status make_layout(const xy_config *c, Layout *lo) {
@@ -76,6 +77,8 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
   lo->off_rplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
   lo->off_dplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
   lo->off_edge = take(static_cast<size_t>(lo->ntiles) * (2 * ty + 64) * sizeof(uint32_t));
+  lo->off_links = take(static_cast<size_t>(lo->ntiles) * (ty + 32) * sizeof(uint32_t));
+  lo->off_link_count = take(static_cast<size_t>(lo->ntiles) * sizeof(uint32_t));
   lo->off_coin = take((n / 32 + 2) * sizeof(uint32_t));
   lo->off_wave = take(static_cast<size_t>(c->L) * 8);
   lo->total = off;
@@ -102,6 +105,8 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.rplane = reinterpret_cast<uint32_t *>(ws + lo.off_rplane);
   d.dplane = reinterpret_cast<uint32_t *>(ws + lo.off_dplane);
   d.edge = reinterpret_cast<uint32_t *>(ws + lo.off_edge);
+  d.links = reinterpret_cast<uint32_t *>(ws + lo.off_links);
+  d.link_count = reinterpret_cast<uint32_t *>(ws + lo.off_link_count);
   d.coin = reinterpret_cast<uint32_t *>(ws + lo.off_coin);
   d.xi = cfg->measure_xi ? 1u : 0u;
   d.wolff = cfg->update == XY_UPDATE_WOLFF ? 1u : 0u;

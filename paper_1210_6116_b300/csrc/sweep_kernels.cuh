@@ -48,6 +48,7 @@ constexpr uint32_t kFindCap = 1u << 22;  // bound on any global find / union loo
 // error bits recorded in DevState::err
 constexpr uint32_t kErrFindCap = 1u;
 constexpr uint32_t kErrUnionCap = 2u;
+constexpr uint32_t kErrLinkCap = 4u;  // more links than edge items (cannot happen)
 
 // Fixed-point scale of the observable sums: each FP32 term in [-1, 1] is
 // rounded to a multiple of 2^-22 and summed exactly in integers.
@@ -96,6 +97,8 @@ struct LatDesc {
   uint32_t *label;
   uint32_t *rplane, *dplane;
   uint32_t *edge;  // per tile: labels of its left/right columns, top/bottom rows
+  uint32_t *links;       // per tile, TY + 32 slots: tile roots its edge items linked
+  uint32_t *link_count;  // per tile: the slots used this sweep (reset by K1)
   uint32_t *coin;
   long long *acc;
   DevState *st;
@@ -323,8 +326,13 @@ __device__ __forceinline__ uint32_t gfind_ro(const uint32_t *lab, uint32_t a,
   return a;
 }
 
+// A successful link of root a is appended to the calling tile's link slots
+// (at most one per call, so the tile's edge-item count bounds them; one
+// counter per tile keeps the appends from piling onto one address):
+// k_compress jumps exactly those roots.
 __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
-                                       DevState *st) {
+                                       DevState *st, uint32_t *links, uint32_t *count,
+                                       uint32_t cap) {
   a = gfind_halve(lab, a, st);
   b = gfind_halve(lab, b, st);
   for (uint32_t it = 0; a != b; ++it) {
@@ -338,7 +346,12 @@ __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
       b = tmp;
     }
     const uint32_t old = atomicCAS(lab + a, a, b);
-    if (old == a) return;
+    if (old == a) {
+      const uint32_t k = atomicAdd(count, 1u);
+      if (k < cap) links[k] = a;
+      else atomicOr(&st->err, kErrLinkCap);
+      return;
+    }
     a = gfind_halve(lab, old, st);
     b = gfind_halve(lab, b, st);
   }
@@ -460,6 +473,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     const uint32_t rmask = (g.w >= 32u) ? 0x7FFFFFFFu : ((1u << (g.w - 1u)) - 1u);
     const uint64_t tbase = static_cast<uint64_t>(tile) * TY;
 
+    if (threadIdx.x == 0) d.link_count[tile] = 0u;  // the merge appends from 0
     uint32_t lab_prev = kNoRoot, D_prev = 0u;
     uint32_t labs[B];
     if (!FROM_PLANES) {
@@ -682,7 +696,7 @@ __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
 // inactive, so every match sees all 32.
 struct EdgeItem {
   const LatDesc *d;
-  uint32_t rep, ta, tb;
+  uint32_t rep, tile, ta, tb;
   bool act;
 };
 
@@ -700,6 +714,7 @@ __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
   e.rep = find_rep(prefix, nrep, work);
   e.d = descs + e.rep;
   const uint32_t tile = work - __ldg(prefix + e.rep);
+  e.tile = tile;
   uint64_t ea = 0, eb = 0;
   e.act = item < total && edge_bond<TY>(*e.d, tile, j, &ea, &eb);
   e.ta = e.act ? __ldg(e.d->edge + ea) : 0u;
@@ -725,13 +740,15 @@ __global__ void __launch_bounds__(kThreads)
   const EdgeItem e = edge_item<TY>(descs, prefix, nrep, nwork);
   const unsigned long long key =
       e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
-  if (group_leader(key, e.rep) && e.act) gunion(e.d->label, e.ta, e.tb, e.d->st);
+  if (group_leader(key, e.rep) && e.act)
+    gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u),
+           e.d->link_count + e.tile, TY + 32u);
 }
 
-// K3: after all unions, every merged tile root re-points at its grandparent
-// until its parent is a root.  All merged tile roots jump concurrently, so a
-// chain of length d collapses in O(log d) steps per node instead of a walk of
-// length d.  Only ancestors are ever written and roots no longer change.
+// Pointer jumping: x re-points at its grandparent until its parent is a
+// root.  When all linked roots jump concurrently, a chain of length d
+// collapses in O(log d) steps per node instead of a walk of length d.  Only
+// ancestors are ever written and roots no longer change.
 __device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st) {
   for (uint32_t it = 0; it < kFindCap; ++it) {
     const uint32_t p = __ldcg(lab + x);
@@ -743,22 +760,25 @@ __device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st) {
   atomicOr(&st->err, kErrFindCap);
 }
 
-
+// K3: every root the merge linked jumps (concurrently with the others) until
+// its parent is a root.  Every entry the merge changed is such a root's: the
+// link itself, or path halving, which only re-points nodes that already have
+// a parent.  Thread j of a tile's edge items takes the tile's j-th link.
 template <int TY>
 __global__ void __launch_bounds__(kThreads)
     k_compress(const LatDesc *__restrict__ descs,
                const uint32_t *__restrict__ prefix, uint32_t nrep,
                uint32_t nwork) {
-  if (nwork == 0u) return;
-  // the tile roots of both endpoints: every entry the merge changed belongs
-  // to such a root (finds and links start from them and only reach their
-  // ancestors, which are such roots too).  Repeated jumps of one root are
-  // cheap here, cheaper than grouping them as the merge does.
-  const EdgeItem e = edge_item<TY>(descs, prefix, nrep, nwork);
-  if (e.act) {
-    jump(e.d->label, e.ta, e.d->st);
-    jump(e.d->label, e.tb, e.d->st);
-  }
+  const uint64_t item = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
+  const uint64_t per = TY + 32;
+  if (item >= static_cast<uint64_t>(nwork) * per) return;
+  const uint32_t work = static_cast<uint32_t>(item / per);
+  const uint32_t j = static_cast<uint32_t>(item % per);
+  const uint32_t rep = find_rep(prefix, nrep, work);
+  const LatDesc &d = descs[rep];
+  const uint32_t tile = work - __ldg(prefix + rep);
+  if (j < __ldcg(d.link_count + tile))
+    jump(d.label, __ldcg(d.links + static_cast<uint64_t>(tile) * per + j), d.st);
 }
 
 // ---------------------------------------------------------------------------

@@ -9,10 +9,10 @@
 // else comes from `g_label_scratch` below.
 //
 // The scratch array is a file-scope __device__ array, so every GPU that
-// loads this library holds it (about 0.79 MB) until the process exits.  All
+// loads this library holds it (about 1.05 MB) until the process exits.  All
 // calls share it and it keeps the contents of the last call: every call
 // rewrites the parts it reads (descriptor, state word, bit planes, tile edge
-// table) before using them, and calls whose work overlaps on the GPU (two streams, or two
+// table, link list) before using them, and calls whose work overlaps on the GPU (two streams, or two
 // host threads at once) race on it and give wrong labels.
 #include <cuda_runtime.h>
 
@@ -42,8 +42,11 @@ constexpr size_t kOffState = 512;
 constexpr size_t kOffRplane = 1024;
 constexpr size_t kOffDplane = kOffRplane + kPlaneWords * sizeof(uint32_t);
 constexpr size_t kOffEdge = kOffDplane + kPlaneWords * sizeof(uint32_t);
-constexpr size_t kScratchBytes =
+constexpr size_t kOffLinks =
     kOffEdge + static_cast<size_t>(kStaticMaxTiles) * edge_words<kStaticTile>() * sizeof(uint32_t);
+constexpr size_t kOffLinkCount =
+    kOffLinks + static_cast<size_t>(kStaticMaxTiles) * (kStaticTile + 32) * sizeof(uint32_t);
+constexpr size_t kScratchBytes = kOffLinkCount + static_cast<size_t>(kStaticMaxTiles) * sizeof(uint32_t);
 static_assert(sizeof(LatDesc) <= 256 && sizeof(DevState) <= 512, "scratch layout");
 
 // The scratch memory.  In host code this name is only a stand-in for the
@@ -142,6 +145,8 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   d.rplane = reinterpret_cast<uint32_t *>(scratch + kOffRplane);
   d.dplane = reinterpret_cast<uint32_t *>(scratch + kOffDplane);
   d.edge = reinterpret_cast<uint32_t *>(scratch + kOffEdge);
+  d.links = reinterpret_cast<uint32_t *>(scratch + kOffLinks);
+  d.link_count = reinterpret_cast<uint32_t *>(scratch + kOffLinkCount);
   d.st = reinterpret_cast<DevState *>(scratch + kOffState);
   LatDesc *d_desc = reinterpret_cast<LatDesc *>(scratch + kOffDesc);
   uint32_t *d_prefix = reinterpret_cast<uint32_t *>(scratch + kOffPrefix);
