@@ -222,12 +222,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"SW sweep, 2D XY, L={L} periodic ({N} spins), beta={beta}, "
-                                   "FP32 angles, Philox random start",
-                       "L": L, "beta": beta, "tile": f"32x{lat.cfg.tile_y or 'auto'}",
-                       "thresholds": "fp64-exact" if args.exact else "fp32",
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "working set 204 MB > 126 MB L2; no flush"},
+            "config": bench_config(args, ws),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -548,6 +543,18 @@ def cpu_baseline(args):
             "host_cores_available": os.cpu_count()}
 
 
+def bench_config(args, ws: int) -> dict:
+    """The workload both arms report (the reference arm times a bounded
+    sample of it, described in its cpu_baseline)."""
+    L, N = args.L, args.L * args.L
+    return {"workload": f"SW sweep, 2D XY, L={L} periodic ({N} spins), beta={args.beta}, "
+                        "FP32 angles, Philox random start",
+            "L": L, "beta": args.beta, "tile": f"32x{args.tile_y or 'auto'}",
+            "thresholds": "fp64-exact" if args.exact else "fp32",
+            "parallelism": f"replicas x{ws}",
+            "l2": f"working set {N * 12.75 / 1e6:.0f} MB > 126 MB L2; no flush"}
+
+
 def run_reference(args):
     """The oracle timed as the reference arm (rank 0 only)."""
     ws, rank, _ = _dist()
@@ -574,8 +581,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"SW sweep, 2D XY, L={args.L} periodic, beta={args.beta} "
-                               f"(timed on an L={L_s} sample)", "L": args.L, "beta": args.beta},
+        "config": bench_config(args, ws),
         "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
