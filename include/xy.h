@@ -240,6 +240,18 @@ xy_status xy_get_band_stats(xy_lattice *h, uint64_t *n_fp64,
 xy_status xy_run_host(xy_lattice *h, const void *host_angles_in,
                       uint32_t n_sweeps, xy_obs *host_obs,
                       void *host_angles_out);
+/* xy_run_host without the final synchronisation: the copies and sweeps are
+ * enqueued on the lattice's stream and the call returns at once, so a caller
+ * can overlap one lattice's copies with another's sweeps (pinned host
+ * buffers make the copies asynchronous).  The host buffers must stay valid,
+ * and host_obs / host_angles_out unread, until xy_sync returns; device-side
+ * errors are reported by xy_sync. */
+xy_status xy_run_host_async(xy_lattice *h, const void *host_angles_in,
+                            uint32_t n_sweeps, xy_obs *host_obs,
+                            void *host_angles_out);
+/* Wait for everything enqueued on the lattice's stream; XY_ETIMEOUT if a
+ * device loop hit its bound since the last check. */
+xy_status xy_sync(xy_lattice *h);
 
 /* ---- kernel timing ------------------------------------------------------- */
 /* Kernel index of xy_kernel_times: 0 bond+tile label, 1 edge merge,

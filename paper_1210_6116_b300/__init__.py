@@ -52,8 +52,8 @@ EXPORTS = (
     "xy_last_error", "xy_workspace_size", "xy_init", "xy_sweep", "xy_pcc_step",
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
     "xy_get_bonds", "xy_get_labels", "xy_get_sites", "xy_label_bonds", "xy_get_band_stats",
-    "xy_save",
-    "xy_load", "xy_run_host", "xy_profile", "xy_profile_read", "xy_label_bonds_static",
+    "xy_save", "xy_load", "xy_run_host", "xy_run_host_async", "xy_sync", "xy_profile",
+    "xy_profile_read", "xy_label_bonds_static",
     "xy_engine_workspace_size", "xy_engine_create", "xy_engine_admit", "xy_engine_retire",
     "xy_engine_step", "xy_engine_measure", "xy_engine_get_angles", "xy_engine_get_state",
     "xy_engine_destroy",
@@ -130,6 +130,8 @@ def load_library() -> ctypes.CDLL:
         "xy_save": (I, [P, P, P]),
         "xy_load": (I, [P, P, ctypes.c_size_t]),
         "xy_run_host": (I, [P, P, U32, P, P]),
+        "xy_run_host_async": (I, [P, P, ctypes.c_uint32, P, P]),
+        "xy_sync": (I, [P]),
         "xy_profile": (I, [P, I]),
         "xy_profile_read": (I, [P, P]),
         "xy_label_bonds_static": (I, [U32, P, P, P, P, I]),
@@ -320,6 +322,16 @@ class Lattice:
         pin = (lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data))
         _check(load_library().xy_run_host(self.handle, pin(angles_in), n_sweeps,
                                           pin(obs_out), pin(angles_out)))
+
+    def run_host_async(self, angles_in, n_sweeps: int, obs_out=None, angles_out=None):
+        """xy_run_host_async: enqueue only; the buffers must stay alive and
+        unread until sync()."""
+        pin = (lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data))
+        _check(load_library().xy_run_host_async(self.handle, pin(angles_in), n_sweeps,
+                                                pin(obs_out), pin(angles_out)))
+
+    def sync(self):
+        _check(load_library().xy_sync(self.handle))
 
     def profile(self, enable: bool, every: int = 1):
         """Time the kernels of every `every`-th sweep with CUDA events (the

@@ -390,8 +390,10 @@ xy_status xy_destroy(xy_lattice *h) {
   return XY_OK;
 }
 
-xy_status xy_run_host(xy_lattice *h, const void *host_angles_in, uint32_t n_sweeps,
-                      xy_obs *host_obs, void *host_angles_out) {
+namespace {
+// the copies and sweeps of xy_run_host, enqueued on the lattice's stream
+xy_status run_host_enqueue(xy_lattice *h, const void *host_angles_in, uint32_t n_sweeps,
+                           xy_obs *host_obs, void *host_angles_out) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
   const size_t ab = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
   // the angle buffer the next sweep reads is theta[cur]; cur flips once per
@@ -418,6 +420,25 @@ xy_status xy_run_host(xy_lattice *h, const void *host_angles_in, uint32_t n_swee
   if (host_angles_out)
     XY_CUDA(cudaMemcpyAsync(host_angles_out, h->desc.theta[cur1], ab, cudaMemcpyDeviceToHost,
                             h->stream));
+  return XY_OK;
+}
+}  // namespace
+
+xy_status xy_run_host(xy_lattice *h, const void *host_angles_in, uint32_t n_sweeps,
+                      xy_obs *host_obs, void *host_angles_out) {
+  const xy_status s = run_host_enqueue(h, host_angles_in, n_sweeps, host_obs, host_angles_out);
+  if (s != XY_OK) return s;
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+xy_status xy_run_host_async(xy_lattice *h, const void *host_angles_in, uint32_t n_sweeps,
+                            xy_obs *host_obs, void *host_angles_out) {
+  return run_host_enqueue(h, host_angles_in, n_sweeps, host_obs, host_angles_out);
+}
+
+xy_status xy_sync(xy_lattice *h) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
   XY_CUDA(cudaStreamSynchronize(h->stream));
   return check_device_error(h);
 }

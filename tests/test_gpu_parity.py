@@ -352,3 +352,22 @@ def test_bench_size_one_sweep_full_parity(orc):
     rec_xi = lat_xi.measure()
     np.testing.assert_array_equal(lat_xi.get_angles(), th)
     assert not obs_close(rec_dict(rec_xi[0]), orc.measure(th, L, L, beta), L * L, beta, xi=True)
+
+
+def test_run_host_async_equals_run_host():
+    """xy_run_host_async + xy_sync on a lattice with its own stream gives the
+    records and angles of xy_run_host, step for step."""
+    import torch
+    L = 256
+    a = _lat(L, 1.1, 31)
+    b = _lat(L, 1.1, 31, stream=torch.cuda.Stream())
+    th = synth.angles(L * L, seed=5)
+    for step in range(4):
+        ra, rb = np.zeros(2, xy.OBS_DTYPE), np.zeros(2, xy.OBS_DTYPE)
+        oa, ob = np.zeros(L * L, np.float32), np.zeros(L * L, np.float32)
+        a.run_host(th, 2, ra, oa)
+        b.run_host_async(th, 2, rb, ob)
+        b.sync()
+        np.testing.assert_array_equal(ra, rb)
+        np.testing.assert_array_equal(oa, ob)
+        th = oa
