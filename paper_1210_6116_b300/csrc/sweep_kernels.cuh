@@ -217,6 +217,16 @@ __device__ __forceinline__ double project64(double th, double cphi,
   return __dadd_rn(__dmul_rn(c, cphi), __dmul_rn(s, sphi));
 }
 
+// Programmatic dependent launch: let the next kernel on the stream be
+// scheduled once every block of this grid runs, and wait for the previous
+// kernel's grid (and its memory) before touching anything it writes.  Both
+// are no-ops for a kernel launched without the attribute.  Every sweep
+// kernel calls this before its first read of mutable data.
+__device__ __forceinline__ void pdl_prologue() {
+  cudaTriggerProgrammaticLaunchCompletion();
+  cudaGridDependencySynchronize();
+}
+
 __device__ __forceinline__ uint32_t find_rep(const uint32_t *__restrict__ pre,
                                              uint32_t nrep, uint32_t work) {
   uint32_t lo = 0, hi = nrep;
@@ -447,6 +457,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     k_bond_label(const LatDesc *__restrict__ descs,
                  const uint32_t *__restrict__ prefix, uint32_t nrep,
                  uint32_t nwork) {
+  pdl_prologue();
   constexpr int B = TY / kWarps;  // rows per band
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *par = reinterpret_cast<uint32_t *>(smem);
@@ -733,6 +744,7 @@ __global__ void __launch_bounds__(kThreads)
     k_merge(const LatDesc *__restrict__ descs,
             const uint32_t *__restrict__ prefix, uint32_t nrep,
             uint32_t nwork) {
+  pdl_prologue();
   if (nwork == 0u) return;
   // start from the tile roots (from the edge table): labels of non-root sites
   // are never written here, so after the merge every site still points at
@@ -769,6 +781,7 @@ __global__ void __launch_bounds__(kThreads)
     k_compress(const LatDesc *__restrict__ descs,
                const uint32_t *__restrict__ prefix, uint32_t nrep,
                uint32_t nwork) {
+  pdl_prologue();
   const uint64_t item = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
   const uint64_t per = TY + 32;
   if (item >= static_cast<uint64_t>(nwork) * per) return;
@@ -816,6 +829,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
                    uint32_t nwork) {
+  pdl_prologue();
   constexpr int B = TY / kWarps;
   __shared__ long long red[kWarps][EXT ? 15 : 6];  // EXT: 14 sums + flip count
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1077,7 +1091,8 @@ static __global__ void __launch_bounds__(kFinalizeThreads)
   // under a thousand instructions when each field was loaded where it was
   // used), so everything it reads is loaded in one batch: the descriptor and
   // the state as whole structs, then the accumulator slots beside the state.
-  const LatDesc d = descs[rep];
+  const LatDesc d = descs[rep];  // static: loaded before the wait
+  pdl_prologue();
   DevState *st = d.st;
   const DevState s0 = *st;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -83,6 +83,27 @@ cudaError_t mark(xy_lattice *h) {
   return cudaEventRecord(h->events[h->ev_used++], h->stream);
 }
 
+// Sweep kernels go out with programmatic dependent launch (each waits for
+// its predecessor inside the kernel, see pdl_prologue), which hides the
+// launch and ramp-up of every kernel behind the one before it.
+constexpr bool kUsePdl = true;
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = kUsePdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <int TY, typename AT, bool EXACT>
 cudaError_t launch_sweep_t(xy_lattice *h) {
   h->prof_this = h->prof != 0 && h->prof_count++ % h->prof == 0;
@@ -94,32 +115,36 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
     if (e != cudaSuccess) return e;
   }
   if ((e = mark(h)) != cudaSuccess) return e;
-  k_bond_label<TY, AT, EXACT, false>
-      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+  const LatDesc *dd = h->d_desc;
+  const uint32_t *pre = h->d_prefix;
+  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false>, nw, kThreads, bond_label_smem<TY>(), s,
+                      dd, pre, 1u, nw)) != cudaSuccess)
+    return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if ((e = launch_pdl(k_merge<TY>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
-  k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  if ((e = launch_pdl(k_compress<TY>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   // the extended K4 for chik sums or Wolff; canonical labels only for the
   // last sweep of an xy_sweep / xy_pcc_step call
   const bool ext = h->desc.xi || h->desc.wolff;
   if (ext && h->write_labels)
-    k_flip_measure<TY, AT, false, true, true>
-        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, true, true>, nw, kThreads, flip_smem<TY>(), s,
+                   dd, pre, 1u, nw);
   else if (ext)
-    k_flip_measure<TY, AT, false, true, false>
-        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, true, false>, nw, kThreads, flip_smem<TY>(), s,
+                   dd, pre, 1u, nw);
   else if (h->write_labels)
-    k_flip_measure<TY, AT, false, false, true>
-        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, false, true>, nw, kThreads, flip_smem<TY>(), s,
+                   dd, pre, 1u, nw);
   else
-    k_flip_measure<TY, AT, false, false, false>
-        <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, false, false>, nw, kThreads, flip_smem<TY>(), s,
+                   dd, pre, 1u, nw);
+  if (e != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
-  k_finalize<<<1, kFinalizeThreads, 0, s>>>(h->d_desc, 1);
+  if ((e = launch_pdl(k_finalize, 1u, kFinalizeThreads, 0, s, dd, 1u)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
