@@ -19,6 +19,7 @@
 #include "../../include/xy.h"
 #include "layout.cuh"
 #include "sweep_kernels.cuh"
+#include "launch.cuh"
 
 using namespace xyk;
 
@@ -81,27 +82,6 @@ cudaError_t mark(xy_lattice *h) {
     h->events.push_back(e);
   }
   return cudaEventRecord(h->events[h->ev_used++], h->stream);
-}
-
-// Sweep kernels go out with programmatic dependent launch (each waits for
-// its predecessor inside the kernel, see pdl_prologue), which hides the
-// launch and ramp-up of every kernel behind the one before it.
-constexpr bool kUsePdl = true;
-
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), uint32_t grid, uint32_t block, size_t smem,
-                       cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = kUsePdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 template <int TY, typename AT, bool EXACT>

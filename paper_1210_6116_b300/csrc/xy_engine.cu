@@ -24,6 +24,7 @@
 #include "../../include/xy.h"
 #include "layout.cuh"
 #include "sweep_kernels.cuh"
+#include "launch.cuh"
 
 using namespace xyk;
 
@@ -58,18 +59,20 @@ struct Slot {
 template <int TY, typename AT, bool EXACT>
 void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uint32_t nw,
                 bool ext, cudaStream_t s) {
-  k_bond_label<TY, AT, EXACT, false>
-      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(descs, prefix, nrep, nw);
+  launch_pdl(k_bond_label<TY, AT, EXACT, false>, nw, kThreads, bond_label_smem<TY>(), s, descs,
+             prefix, nrep, nw);
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  k_merge<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
-  k_compress<TY><<<eb, kThreads, 0, s>>>(descs, prefix, nrep, nw);
+  launch_pdl(k_merge<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
+  launch_pdl(k_compress<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
-    k_flip_measure<TY, AT, false, true, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
+    launch_pdl(k_flip_measure<TY, AT, false, true, false>, nw, kThreads, flip_smem<TY>(), s, descs,
+               prefix, nrep, nw);
   else
-    k_flip_measure<TY, AT, false, false, false><<<nw, kThreads, flip_smem<TY>(), s>>>(descs, prefix, nrep, nw);
-  k_finalize<<<nrep, kFinalizeThreads, 0, s>>>(descs, nrep);
+    launch_pdl(k_flip_measure<TY, AT, false, false, false>, nw, kThreads, flip_smem<TY>(), s,
+               descs, prefix, nrep, nw);
+  launch_pdl(k_finalize, nrep, kFinalizeThreads, 0, s, descs, nrep);
 }
 
 template <typename AT, bool EXACT>
