@@ -28,17 +28,28 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> Path:
+    """Compile the three translation units in parallel (one nvcc each), then
+    link them into libxy.so."""
     if not force and not needs_build():
         return LIB
     tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
-    cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC", "-diag-suppress", "128",
-           "-I", str(ROOT / "include"),
-           str(SRC / "xy_api.cu"), str(SRC / "xy_engine.cu"),
-           str(SRC / "xy_static.cu"), "-o", str(tmp)]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+             "-diag-suppress", "128", "-I", str(ROOT / "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.insert(0, "-Xptxas=-v")
+    objs, procs = [], []
+    for name in ("xy_api.cu", "xy_engine.cu", "xy_static.cu"):
+        obj = LIB.parent / f".{name[:-3]}.{os.getpid()}.o"
+        objs.append(obj)
+        procs.append(subprocess.Popen(["nvcc", *flags, "-c", str(SRC / name), "-o", str(obj)]))
+    try:
+        codes = [pr.wait() for pr in procs]
+        if any(codes):
+            raise subprocess.CalledProcessError(max(codes), "nvcc -c")
+        subprocess.run(["nvcc", *ARCH, "-shared", *map(str, objs), "-o", str(tmp)], check=True)
+    finally:
+        for obj in objs:
+            obj.unlink(missing_ok=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -242,15 +242,18 @@ struct Tile {
   uint32_t x0, y0, w, h, xh, yh;
 };
 
-template <int TY>
+// FULL: every tile of the lattice is a whole 32 x TY (L a multiple of 32 and
+// of TY), so width and height are compile-time constants and the ragged-edge
+// tests of the kernels fold away.
+template <int TY, bool FULL = false>
 __device__ __forceinline__ Tile tile_geom(uint32_t L, uint32_t ntx,
                                           uint32_t tile) {
   Tile g;
   const uint32_t tx = tile % ntx, ty = tile / ntx;
   g.x0 = tx * 32u;
   g.y0 = ty * static_cast<uint32_t>(TY);
-  g.w = min(32u, L - g.x0);
-  g.h = min(static_cast<uint32_t>(TY), L - g.y0);
+  g.w = FULL ? 32u : min(32u, L - g.x0);
+  g.h = FULL ? static_cast<uint32_t>(TY) : min(static_cast<uint32_t>(TY), L - g.y0);
   g.xh = (g.x0 + g.w == L) ? 0u : g.x0 + g.w;  // column right of the tile
   g.yh = (g.y0 + g.h == L) ? 0u : g.y0 + g.h;  // row below the tile
   return g;
@@ -452,7 +455,7 @@ constexpr size_t bond_label_smem() {
 // ---------------------------------------------------------------------------
 // K1: projection + bonds + coins + tile labels
 // ---------------------------------------------------------------------------
-template <int TY, typename AT, bool EXACT, bool FROM_PLANES>
+template <int TY, typename AT, bool EXACT, bool FROM_PLANES, bool FULL = false>
 __global__ void __launch_bounds__(kThreads, 4)
     k_bond_label(const LatDesc *__restrict__ descs,
                  const uint32_t *__restrict__ prefix, uint32_t nrep,
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     const LatDesc &d = descs[rep];
     const uint32_t tile = work - __ldg(prefix + rep);
     const uint32_t L = d.L;
-    const Tile g = tile_geom<TY>(L, d.ntx, tile);
+    const Tile g = tile_geom<TY, FULL>(L, d.ntx, tile);
     DevState *st = d.st;
     uint32_t npairs = 0u;
     const uint32_t r0 = static_cast<uint32_t>(warp) * B;
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 4)
           sR[r] = Rw;
           sD[r] = Dw;
           const uint32_t i0 = (g.y0 + r) * L + g.x0;
-          if (!d.ragged) {
+          if (FULL || !d.ragged) {
             d.coin[i0 >> 5] = Cw;
           } else if (Cw) {
             const uint32_t off = i0 & 31u;
@@ -824,7 +827,8 @@ constexpr size_t flip_smem() {
 // read back, and always with LABELS_ONLY); otherwise the next sweep's K1
 // overwrites them, and leaving the store out saves ~8 us per sweep at
 // L = 4096.
-template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false, bool WL = true>
+template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false, bool WL = true,
+          bool FULL = false>
 __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
@@ -839,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     const LatDesc &d = descs[rep];
     const uint32_t tile = work - __ldg(prefix + rep);
     const uint32_t L = d.L;
-    const Tile g = tile_geom<TY>(L, d.ntx, tile);
+    const Tile g = tile_geom<TY, FULL>(L, d.ntx, tile);
     DevState *st = d.st;
     const uint32_t cur = st->cur;
     const float c32 = st->c32;

@@ -84,7 +84,7 @@ cudaError_t mark(xy_lattice *h) {
   return cudaEventRecord(h->events[h->ev_used++], h->stream);
 }
 
-template <int TY, typename AT, bool EXACT>
+template <int TY, typename AT, bool EXACT, bool FULL>
 cudaError_t launch_sweep_t(xy_lattice *h) {
   h->prof_this = h->prof != 0 && h->prof_count++ % h->prof == 0;
   const uint32_t nw = h->lo.ntiles;
@@ -97,7 +97,7 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   if ((e = mark(h)) != cudaSuccess) return e;
   const LatDesc *dd = h->d_desc;
   const uint32_t *pre = h->d_prefix;
-  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false>, nw, kThreads, bond_label_smem<TY>(), s,
+  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL>, nw, kThreads, bond_label_smem<TY>(), s,
                       dd, pre, 1u, nw)) != cudaSuccess)
     return e;
   if ((e = mark(h)) != cudaSuccess) return e;
@@ -111,16 +111,16 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   // last sweep of an xy_sweep / xy_pcc_step call
   const bool ext = h->desc.xi || h->desc.wolff;
   if (ext && h->write_labels)
-    e = launch_pdl(k_flip_measure<TY, AT, false, true, true>, nw, kThreads, flip_smem<TY>(), s,
+    e = launch_pdl(k_flip_measure<TY, AT, false, true, true, FULL>, nw, kThreads, flip_smem<TY>(), s,
                    dd, pre, 1u, nw);
   else if (ext)
-    e = launch_pdl(k_flip_measure<TY, AT, false, true, false>, nw, kThreads, flip_smem<TY>(), s,
+    e = launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
                    dd, pre, 1u, nw);
   else if (h->write_labels)
-    e = launch_pdl(k_flip_measure<TY, AT, false, false, true>, nw, kThreads, flip_smem<TY>(), s,
+    e = launch_pdl(k_flip_measure<TY, AT, false, false, true, FULL>, nw, kThreads, flip_smem<TY>(), s,
                    dd, pre, 1u, nw);
   else
-    e = launch_pdl(k_flip_measure<TY, AT, false, false, false>, nw, kThreads, flip_smem<TY>(), s,
+    e = launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
                    dd, pre, 1u, nw);
   if (e != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
@@ -129,11 +129,22 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   return cudaGetLastError();
 }
 
+// whole tiles only (L a multiple of 32 and of TY): the FULL kernels
+template <int TY, typename AT, bool EXACT>
+cudaError_t launch_exact_full(xy_lattice *h) {
+  const bool full = h->lo.L % 32u == 0u && h->lo.L % static_cast<uint32_t>(TY) == 0u;
+  return full ? launch_sweep_t<TY, AT, EXACT, true>(h) : launch_sweep_t<TY, AT, EXACT, false>(h);
+}
+
 template <int TY, typename AT, bool EXACT>
 cudaError_t set_attrs_t() {
   cudaError_t e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(bond_label_smem<TY>()));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(bond_label_smem<TY>()));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -151,8 +162,8 @@ cudaError_t set_attrs_t() {
 template <int TY, typename AT>
 cudaError_t dispatch_exact(xy_lattice *h, bool attrs) {
   if (h->cfg.threshold_mode == XY_THR_F64)
-    return attrs ? set_attrs_t<TY, AT, true>() : launch_sweep_t<TY, AT, true>(h);
-  return attrs ? set_attrs_t<TY, AT, false>() : launch_sweep_t<TY, AT, false>(h);
+    return attrs ? set_attrs_t<TY, AT, true>() : launch_exact_full<TY, AT, true>(h);
+  return attrs ? set_attrs_t<TY, AT, false>() : launch_exact_full<TY, AT, false>(h);
 }
 
 template <typename AT>

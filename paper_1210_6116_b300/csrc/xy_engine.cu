@@ -56,10 +56,10 @@ struct Slot {
   uint64_t reported = 0;
 };
 
-template <int TY, typename AT, bool EXACT>
+template <int TY, typename AT, bool EXACT, bool FULL>
 void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uint32_t nw,
                 bool ext, cudaStream_t s) {
-  launch_pdl(k_bond_label<TY, AT, EXACT, false>, nw, kThreads, bond_label_smem<TY>(), s, descs,
+  launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL>, nw, kThreads, bond_label_smem<TY>(), s, descs,
              prefix, nrep, nw);
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
@@ -67,23 +67,31 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
   launch_pdl(k_compress<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
-    launch_pdl(k_flip_measure<TY, AT, false, true, false>, nw, kThreads, flip_smem<TY>(), s, descs,
+    launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s, descs,
                prefix, nrep, nw);
   else
-    launch_pdl(k_flip_measure<TY, AT, false, false, false>, nw, kThreads, flip_smem<TY>(), s,
+    launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
                descs, prefix, nrep, nw);
   launch_pdl(k_finalize, nrep, kFinalizeThreads, 0, s, descs, nrep);
 }
 
+template <typename AT, bool EXACT, bool FULL>
+void launch_ty_full(uint32_t TY, const LatDesc *descs, const uint32_t *prefix, uint32_t nrep,
+                    uint32_t nw, bool ext, cudaStream_t s) {
+  switch (TY) {
+    case 16: launch_all<16, AT, EXACT, FULL>(descs, prefix, nrep, nw, ext, s); break;
+    case 32: launch_all<32, AT, EXACT, FULL>(descs, prefix, nrep, nw, ext, s); break;
+    case 64: launch_all<64, AT, EXACT, FULL>(descs, prefix, nrep, nw, ext, s); break;
+    default: launch_all<128, AT, EXACT, FULL>(descs, prefix, nrep, nw, ext, s); break;
+  }
+}
+
+// full: every lattice of the table is made of whole tiles (the FULL kernels)
 template <typename AT, bool EXACT>
 void launch_ty(uint32_t TY, const LatDesc *descs, const uint32_t *prefix, uint32_t nrep,
-               uint32_t nw, bool ext, cudaStream_t s) {
-  switch (TY) {
-    case 16: launch_all<16, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
-    case 32: launch_all<32, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
-    case 64: launch_all<64, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
-    default: launch_all<128, AT, EXACT>(descs, prefix, nrep, nw, ext, s); break;
-  }
+               uint32_t nw, bool ext, bool full, cudaStream_t s) {
+  if (full) launch_ty_full<AT, EXACT, true>(TY, descs, prefix, nrep, nw, ext, s);
+  else launch_ty_full<AT, EXACT, false>(TY, descs, prefix, nrep, nw, ext, s);
 }
 
 }  // namespace
@@ -112,18 +120,21 @@ size_t table_bytes(uint32_t max_slots) {
 }
 
 void launch_table(xy_engine *e, cudaStream_t s) {
-  bool ext = false;
-  for (const LatDesc &d : e->h_descs) ext = ext || d.xi || d.wolff;
+  bool ext = false, full = true;
+  for (const LatDesc &d : e->h_descs) {
+    ext = ext || d.xi || d.wolff;
+    full = full && d.L % 32u == 0u && d.L % e->TY == 0u;
+  }
   const bool ex = e->thr == XY_THR_F64;
   if (e->dtype == XY_F32) {
-    if (ex) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
-    else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
+    if (ex) launch_ty<float, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, full, s);
+    else launch_ty<float, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, full, s);
   } else if (e->dtype == XY_F16) {
-    if (ex) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
-    else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
+    if (ex) launch_ty<__half, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, full, s);
+    else launch_ty<__half, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, full, s);
   } else {
-    if (ex) launch_ty<uint16_t, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
-    else launch_ty<uint16_t, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, s);
+    if (ex) launch_ty<uint16_t, true>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, full, s);
+    else launch_ty<uint16_t, false>(e->TY, e->d_descs, e->d_prefix, e->nrep, e->nwork, ext, full, s);
   }
 }
 
