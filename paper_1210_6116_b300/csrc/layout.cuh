@@ -98,6 +98,7 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.rec_cap = lo.rec_cap;
   d.ragged = (lo.L % 32) != 0;
   d.Lmagic = ~0ull / lo.L + 1ull;
+  d.ntx_magic = ~0ull / lo.ntx + 1ull;
   d.inv_n = 1.0 / (static_cast<double>(lo.L) * lo.L);
   d.theta[0] = ws + lo.off_theta0;
   d.theta[1] = ws + lo.off_theta1;

@@ -88,7 +88,8 @@ struct DevState {
 struct LatDesc {
   uint32_t L, ntx, nty, ntiles;
   uint32_t key0, key1, rec_cap, ragged;
-  uint64_t Lmagic;  // ceil(2^64 / L): x / L == umul64hi(x, Lmagic) for x < 2^32
+  uint64_t Lmagic;     // ceil(2^64 / L): x / L == umul64hi(x, Lmagic) for x < 2^32
+  uint64_t ntx_magic;  // ceil(2^64 / ntx) (0 for ntx = 1): the same exact division by ntx
   double inv_n;     // 1 / L^2
   uint32_t xi;     // 1: accumulate the Fourier sums of chik
   uint32_t wolff;  // 1: Wolff single-cluster update (reflect the seed's cluster)
@@ -246,10 +247,14 @@ struct Tile {
 // of TY), so width and height are compile-time constants and the ragged-edge
 // tests of the kernels fold away.
 template <int TY, bool FULL = false>
-__device__ __forceinline__ Tile tile_geom(uint32_t L, uint32_t ntx,
+__device__ __forceinline__ Tile tile_geom(uint32_t L, uint32_t ntx, uint64_t ntx_magic,
                                           uint32_t tile) {
   Tile g;
-  const uint32_t tx = tile % ntx, ty = tile / ntx;
+  // tile / ntx as a multiply-high by ceil(2^64 / ntx): exact for 32-bit
+  // operands (the error term stays below 2^-32 < 1 / ntx); ceil(2^64 / 1)
+  // does not fit, so one tile column is its own case (ntx_magic = 0)
+  const uint32_t ty = ntx == 1u ? tile : static_cast<uint32_t>(__umul64hi(tile, ntx_magic));
+  const uint32_t tx = tile - ty * ntx;
   g.x0 = tx * 32u;
   g.y0 = ty * static_cast<uint32_t>(TY);
   g.w = FULL ? 32u : min(32u, L - g.x0);
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     const LatDesc &d = descs[rep];
     const uint32_t tile = work - __ldg(prefix + rep);
     const uint32_t L = d.L;
-    const Tile g = tile_geom<TY, FULL>(L, d.ntx, tile);
+    const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
     DevState *st = d.st;
     uint32_t npairs = 0u;
     const uint32_t r0 = static_cast<uint32_t>(warp) * B;
@@ -671,20 +676,20 @@ __global__ void __launch_bounds__(kThreads, 4)
 // endpoints.  (Repeated unions of the same two tile roots are grouped in
 // k_merge; a check of the neighbouring bonds here saved fewer of them than
 // its plane loads cost.)
-template <int TY>
+template <int TY, bool FULL>
 __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
                                           uint32_t j, uint64_t *ea,
                                           uint64_t *eb) {
   constexpr uint32_t EW = edge_words<TY>();
   const uint32_t L = d.L;
-  const Tile g = tile_geom<TY>(L, d.ntx, tile);
+  const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
   const uint64_t base = static_cast<uint64_t>(tile) * TY;
   if (j < static_cast<uint32_t>(TY)) {
     if (j >= g.h) return false;
     const uint32_t bit = g.w - 1u;
     if (!((__ldg(d.rplane + base + j) >> bit) & 1u)) return false;
     // the neighbouring tile to the right holds column xh as its column 0
-    const uint32_t tx = tile % d.ntx;
+    const uint32_t tx = g.x0 >> 5;
     const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
     *ea = static_cast<uint64_t>(tile) * EW + TY + j;  // right column, row j
     *eb = static_cast<uint64_t>(tn) * EW + j;         // its left column, row j
@@ -695,8 +700,8 @@ __device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
   const uint32_t D = __ldg(d.dplane + base + g.h - 1u);
   if (!((D >> c) & 1u)) return false;
   // the tile below holds row yh as its row 0, same columns
-  const uint32_t ty = tile / d.ntx;
-  const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tile % d.ntx;
+  const uint32_t ty = g.y0 / static_cast<uint32_t>(TY);
+  const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + (g.x0 >> 5);
   *ea = static_cast<uint64_t>(tile) * EW + 2 * TY + 32 + c;  // bottom row, column c
   *eb = static_cast<uint64_t>(tb) * EW + 2 * TY + c;         // its top row, column c
   return true;
@@ -714,7 +719,7 @@ struct EdgeItem {
   bool act;
 };
 
-template <int TY>
+template <int TY, bool FULL>
 __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
                                               const uint32_t *__restrict__ prefix,
                                               uint32_t nrep, uint32_t nwork) {
@@ -730,7 +735,7 @@ __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
   const uint32_t tile = work - __ldg(prefix + e.rep);
   e.tile = tile;
   uint64_t ea = 0, eb = 0;
-  e.act = item < total && edge_bond<TY>(*e.d, tile, j, &ea, &eb);
+  e.act = item < total && edge_bond<TY, FULL>(*e.d, tile, j, &ea, &eb);
   e.ta = e.act ? __ldg(e.d->edge + ea) : 0u;
   e.tb = e.act ? __ldg(e.d->edge + eb) : 0u;
   return e;
@@ -742,7 +747,7 @@ __device__ __forceinline__ bool group_leader(unsigned long long key, uint32_t re
   return (threadIdx.x & 31u) == static_cast<unsigned>(__ffs(m) - 1);
 }
 
-template <int TY>
+template <int TY, bool FULL = false>
 __global__ void __launch_bounds__(kThreads)
     k_merge(const LatDesc *__restrict__ descs,
             const uint32_t *__restrict__ prefix, uint32_t nrep,
@@ -752,7 +757,7 @@ __global__ void __launch_bounds__(kThreads)
   // start from the tile roots (from the edge table): labels of non-root sites
   // are never written here, so after the merge every site still points at
   // its tile root
-  const EdgeItem e = edge_item<TY>(descs, prefix, nrep, nwork);
+  const EdgeItem e = edge_item<TY, FULL>(descs, prefix, nrep, nwork);
   const unsigned long long key =
       e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
   if (group_leader(key, e.rep) && e.act)
@@ -843,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     const LatDesc &d = descs[rep];
     const uint32_t tile = work - __ldg(prefix + rep);
     const uint32_t L = d.L;
-    const Tile g = tile_geom<TY, FULL>(L, d.ntx, tile);
+    const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
     DevState *st = d.st;
     const uint32_t cur = st->cur;
     const float c32 = st->c32;

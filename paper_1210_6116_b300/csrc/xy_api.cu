@@ -103,7 +103,7 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   if ((e = mark(h)) != cudaSuccess) return e;
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  if ((e = launch_pdl(k_merge<TY>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_merge<TY, FULL>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   if ((e = launch_pdl(k_compress<TY>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;

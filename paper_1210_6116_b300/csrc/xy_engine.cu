@@ -63,7 +63,7 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
              prefix, nrep, nw);
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  launch_pdl(k_merge<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
+  launch_pdl(k_merge<TY, FULL>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
   launch_pdl(k_compress<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags

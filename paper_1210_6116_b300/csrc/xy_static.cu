@@ -104,7 +104,7 @@ __global__ void k_static_pack(const uint8_t *__restrict__ right,
   if (gw >= rows) return;
   const uint32_t tile = static_cast<uint32_t>(gw / kStaticTile);
   const uint32_t r = static_cast<uint32_t>(gw % kStaticTile);
-  const Tile g = tile_geom<kStaticTile>(d.L, d.ntx, tile);
+  const Tile g = tile_geom<kStaticTile>(d.L, d.ntx, d.ntx_magic, tile);
   bool br = false, bd = false;
   if (r < g.h && lane < static_cast<int>(g.w)) {
     const uint64_t i = static_cast<uint64_t>(g.y0 + r) * d.L + g.x0 + lane;
@@ -139,6 +139,7 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   d.Lmagic = ~0ull / L + 1ull;
   d.inv_n = 1.0 / (static_cast<double>(L) * L);
   d.ntx = (L + 31) / 32;
+  d.ntx_magic = ~0ull / d.ntx + 1ull;
   d.nty = (L + kStaticTile - 1) / kStaticTile;
   d.ntiles = d.ntx * d.nty;
   d.label = d_labels;
