@@ -460,8 +460,16 @@ constexpr size_t bond_label_smem() {
 // ---------------------------------------------------------------------------
 // K1: projection + bonds + coins + tile labels
 // ---------------------------------------------------------------------------
+// CTAs per SM: the whole-tile FP32-threshold sweep kernel fits 6 (40
+// registers, no spills; at L = 4096 151 -> 139 us against 4); the general
+// ones keep 4, where more would spill.
+template <int TY, bool EXACT, bool FROM_PLANES, bool FULL>
+constexpr int k1_min_blocks() {
+  return (FULL && !EXACT && !FROM_PLANES && TY <= 64) ? 6 : 4;
+}
+
 template <int TY, typename AT, bool EXACT, bool FROM_PLANES, bool FULL = false>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANES, FULL>()))
     k_bond_label(const LatDesc *__restrict__ descs,
                  const uint32_t *__restrict__ prefix, uint32_t nrep,
                  uint32_t nwork) {
