@@ -680,39 +680,49 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
 // K2: merge across tile edges.  Work item = (tile, j): j < TY is the right
 // edge of tile row j, j >= TY the bottom edge of column j - TY.
 // ---------------------------------------------------------------------------
-// On an active edge bond, *ea and *eb are the edge-table entries of its two
-// endpoints.  (Repeated unions of the same two tile roots are grouped in
-// k_merge; a check of the neighbouring bonds here saved fewer of them than
-// its plane loads cost.)
+// Edge item j of a tile: j < TY is the bond from row j of its right column
+// to the next tile, j >= TY the bond from column j - TY of its bottom row to
+// the tile below.  Returns whether that bond exists and is active, and the
+// tile roots of its two endpoints from the edge table.  The roots are loaded
+// together with the bond's plane word (all three addresses lie inside their
+// arrays whatever the bond), so the chain of dependent loads is one shorter.
+// (Repeated unions of the same two tile roots are grouped in k_merge; a
+// check of the neighbouring bonds here saved fewer of them than its plane
+// loads cost.)
 template <int TY, bool FULL>
-__device__ __forceinline__ bool edge_bond(const LatDesc &d, uint32_t tile,
-                                          uint32_t j, uint64_t *ea,
-                                          uint64_t *eb) {
+__device__ __forceinline__ bool edge_roots(const LatDesc &d, uint32_t tile, uint32_t j,
+                                           uint32_t *ta, uint32_t *tb) {
   constexpr uint32_t EW = edge_words<TY>();
-  const uint32_t L = d.L;
-  const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
+  const Tile g = tile_geom<TY, FULL>(d.L, d.ntx, d.ntx_magic, tile);
   const uint64_t base = static_cast<uint64_t>(tile) * TY;
+  const uint32_t tx = g.x0 >> 5;
+  const uint32_t *plane;
+  uint64_t ea, eb;
+  uint32_t bit;
+  bool valid;
   if (j < static_cast<uint32_t>(TY)) {
-    if (j >= g.h) return false;
-    const uint32_t bit = g.w - 1u;
-    if (!((__ldg(d.rplane + base + j) >> bit) & 1u)) return false;
     // the neighbouring tile to the right holds column xh as its column 0
-    const uint32_t tx = g.x0 >> 5;
     const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
-    *ea = static_cast<uint64_t>(tile) * EW + TY + j;  // right column, row j
-    *eb = static_cast<uint64_t>(tn) * EW + j;         // its left column, row j
-    return true;
+    valid = j < g.h;
+    bit = g.w - 1u;
+    plane = d.rplane + base + j;
+    ea = static_cast<uint64_t>(tile) * EW + TY + j;  // right column, row j
+    eb = static_cast<uint64_t>(tn) * EW + j;         // its left column, row j
+  } else {
+    // the tile below holds row yh as its row 0, same columns
+    const uint32_t c = j - TY;
+    const uint32_t ty = g.y0 / static_cast<uint32_t>(TY);
+    const uint32_t tb_ = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tx;
+    valid = c < g.w;
+    bit = c;
+    plane = d.dplane + base + g.h - 1u;
+    ea = static_cast<uint64_t>(tile) * EW + 2 * TY + 32 + c;  // bottom row, column c
+    eb = static_cast<uint64_t>(tb_) * EW + 2 * TY + c;        // its top row, column c
   }
-  const uint32_t c = j - TY;
-  if (c >= g.w) return false;
-  const uint32_t D = __ldg(d.dplane + base + g.h - 1u);
-  if (!((D >> c) & 1u)) return false;
-  // the tile below holds row yh as its row 0, same columns
-  const uint32_t ty = g.y0 / static_cast<uint32_t>(TY);
-  const uint32_t tb = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + (g.x0 >> 5);
-  *ea = static_cast<uint64_t>(tile) * EW + 2 * TY + 32 + c;  // bottom row, column c
-  *eb = static_cast<uint64_t>(tb) * EW + 2 * TY + c;         // its top row, column c
-  return true;
+  const uint32_t w = __ldg(plane);
+  *ta = __ldg(d.edge + ea);
+  *tb = __ldg(d.edge + eb);
+  return valid && ((w >> bit) & 1u);
 }
 
 // The edge items of one warp (a tile edge, or parts of two for TY = 16 and
@@ -742,10 +752,9 @@ __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
   e.d = descs + e.rep;
   const uint32_t tile = work - __ldg(prefix + e.rep);
   e.tile = tile;
-  uint64_t ea = 0, eb = 0;
-  e.act = item < total && edge_bond<TY, FULL>(*e.d, tile, j, &ea, &eb);
-  e.ta = e.act ? __ldg(e.d->edge + ea) : 0u;
-  e.tb = e.act ? __ldg(e.d->edge + eb) : 0u;
+  const bool bond = edge_roots<TY, FULL>(*e.d, tile, j, &e.ta, &e.tb);
+  e.act = item < total && bond;
+  if (!e.act) e.ta = e.tb = 0u;
   return e;
 }
 
@@ -806,8 +815,11 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t rep = find_rep(prefix, nrep, work);
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
-  if (j < __ldcg(d.link_count + tile))
-    jump(d.label, __ldcg(d.links + static_cast<uint64_t>(tile) * per + j), d.st);
+  // the slot is read together with the count (it lies inside the tile's
+  // slots; past the count it holds an older sweep's entry and is not used)
+  const uint32_t count = __ldcg(d.link_count + tile);
+  const uint32_t x = __ldcg(d.links + static_cast<uint64_t>(tile) * per + j);
+  if (j < count) jump(d.label, x, d.st);
 }
 
 // ---------------------------------------------------------------------------
