@@ -825,10 +825,12 @@ __global__ void __launch_bounds__(kThreads)
 // ---------------------------------------------------------------------------
 // K4: canonical labels, flip, observable sums
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int fix22(float v) {
-  // v in [-1, 1]: v + 3 lies in [2, 4], whose FP32 grid step is 2^-22, so the
-  // bit pattern minus that of 3.0 is round(v * 2^22).
-  return __float_as_int(__fadd_rn(v, 3.0f)) - 0x40400000;
+// Fixed point of a term v in [-1, 1]: v + 3 lies in [2, 4], whose FP32 grid
+// step is 2^-22, so the bit pattern of v + 3 minus that of 3.0 (0x40400000)
+// is round(v * 2^22).  The kernels sum the patterns and take the constant off
+// per summed term afterwards.
+__device__ __forceinline__ uint32_t fix22_bits(float v) {
+  return __float_as_uint(__fadd_rn(v, 3.0f));
 }
 
 template <int TY>
@@ -963,10 +965,13 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     sin_cos<AT>(fc ? reflect<AT>(tc, c32) : tc, &sc, &cc);
     // observable terms of the band's own sites (with d.xi also the Fourier
     // sums of chik: s(r) times (cos, sin)(2 pi x / L) and (2 pi y / L))
+    // Each term's fixed-point value is the bit pattern of v + 3 minus that of
+    // 3.0 (fix22); the patterns are summed modulo 2^32 and the constant is
+    // taken off once per thread below (exact: the true sum fits in 32 bits).
     constexpr int NV = EXT ? 14 : 6;
-    int acc[NV];
+    uint32_t acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0;
+    for (int k = 0; k < NV; ++k) acc[k] = 0u;
     const bool xi = EXT && d.xi != 0u;
     float2 wx = make_float2(0.0f, 0.0f);
     if constexpr (EXT) {
@@ -985,36 +990,49 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       }
       if (col_ok) {
         const float ci = co[k], si = sn[k], cd = co[k + 1], sd = sn[k + 1];
-        acc[0] += fix22(ci);
-        acc[1] += fix22(si);
-        acc[2] += fix22(fmaf(ci, cr, si * sr));
-        acc[3] += fix22(fmaf(si, cr, -(ci * sr)));
-        acc[4] += fix22(fmaf(ci, cd, si * sd));
-        acc[5] += fix22(fmaf(si, cd, -(ci * sd)));
+        acc[0] += fix22_bits(ci);
+        acc[1] += fix22_bits(si);
+        acc[2] += fix22_bits(fmaf(ci, cr, si * sr));
+        acc[3] += fix22_bits(fmaf(si, cr, -(ci * sr)));
+        acc[4] += fix22_bits(fmaf(ci, cd, si * sd));
+        acc[5] += fix22_bits(fmaf(si, cd, -(ci * sd)));
         if constexpr (EXT) {
           if (xi) {
             const float2 wy = __ldg(d.wave + g.y0 + r0 + k);
-            acc[NV - 8] += fix22(ci * wx.x);
-            acc[NV - 7] += fix22(ci * wx.y);
-            acc[NV - 6] += fix22(si * wx.x);
-            acc[NV - 5] += fix22(si * wx.y);
-            acc[NV - 4] += fix22(ci * wy.x);
-            acc[NV - 3] += fix22(ci * wy.y);
-            acc[NV - 2] += fix22(si * wy.x);
-            acc[NV - 1] += fix22(si * wy.y);
+            acc[NV - 8] += fix22_bits(ci * wx.x);
+            acc[NV - 7] += fix22_bits(ci * wx.y);
+            acc[NV - 6] += fix22_bits(si * wx.x);
+            acc[NV - 5] += fix22_bits(si * wx.y);
+            acc[NV - 4] += fix22_bits(ci * wy.x);
+            acc[NV - 3] += fix22_bits(ci * wy.y);
+            acc[NV - 2] += fix22_bits(si * wy.x);
+            acc[NV - 1] += fix22_bits(si * wy.y);
           }
         }
       }
     }
     const int nv = xi ? 14 : 6;
+    // rows this thread summed: the offset of 3.0 comes off once per row
+    const uint32_t rows = col_ok ? nb : 0u;
     long long v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      v[k] = acc[k];
-      if (k < nv) {
+      const int t = static_cast<int>(acc[k] - rows * 0x40400000u);  // |sum| <= B 2^22
+      if constexpr (B <= 8) {
+        // a warp's sum stays within 32 x 8 x 2^22 = 2^30: reduce in 32 bits
+        int w = t;
+        if (k < nv) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-          v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+          for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xFFFFFFFFu, w, off);
+        }
+        v[k] = w;
+      } else {
+        v[k] = t;
+        if (k < nv) {
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1)
+            v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], off);
+        }
       }
     }
     if (lane == 0) {
