@@ -91,7 +91,7 @@ def lib():
             "orc_label_uf": (ctypes.c_long, [_I, _I, _I, _I, _P, _P, _P]),
             "orc_flip_f32": (ctypes.c_long, [_I, _I, _P, _P, _U64, _U32, ctypes.c_float, _P]),
             "orc_flip_f16": (ctypes.c_long, [_I, _I, _P, _P, _U64, _U32, ctypes.c_float, _P]),
-            "orc_coin": (_I, [_U64, _U32, _U32]),
+            "orc_coin": (_I, [_U64, _U32, _I, _U32]),
             "orc_sums_f32": (None, [_I, _I, _I, _I, _P, _P]),
             "orc_sums_f16": (None, [_I, _I, _I, _I, _P, _P]),
             "orc_derive": (None, [_P, _D, _P]),
@@ -218,8 +218,9 @@ def label_uf(right, down, Lx: int, Ly: int, per_x: int = 1, per_y: int = 1):
     return lab, int(comps)
 
 
-def coin(seed: int, t: int, root: int) -> int:
-    return int(lib().orc_coin(seed, t, root))
+def coin(seed: int, t: int, root: int, Lx: int) -> int:
+    """Cluster coin of root site `root` in sweep t of an Lx-wide lattice."""
+    return int(lib().orc_coin(seed, t, Lx, root))
 
 
 def flip(theta: np.ndarray, label: np.ndarray, Lx: int, Ly: int, seed: int, t: int, c32):

@@ -218,8 +218,25 @@ static double bond_probability(double ai, double aj, double beta) {
   return 1.0 - exp(-2.0 * beta * x);
 }
 
+/* The BOND-domain words of site i = y*Lx + x.  One Philox draw serves the
+ * vertical pair of sites (x, 2m) and (x, 2m + 1): counter word 0 is
+ * m*Lx + x.  Row 2m takes words 0 and 1 of the draw, row 2m + 1 words 2 and
+ * 3; the first is the site's right-bond word, the second its down-bond
+ * word.  A bond's uniform comes from bits 31..1 of its word, and bit 0 of
+ * the right-bond word is the site's cluster coin (independent of both
+ * uniforms). */
+static void bond_words(uint64_t seed, uint32_t t, int Lx, uint64_t i,
+                       uint32_t *w_right, uint32_t *w_down) {
+  uint64_t x = i % (uint64_t)Lx, y = i / (uint64_t)Lx;
+  uint64_t c = (y >> 1) * (uint64_t)Lx + x;
+  uint32_t w[4];
+  philox_draw(seed, (uint32_t)c, (uint32_t)(c >> 32), t, ORC_DOM_BOND, w);
+  *w_right = (y & 1u) ? w[2] : w[0];
+  *w_down = (y & 1u) ? w[3] : w[1];
+}
+
 static double uniform_open(uint32_t w) {
-  return ((double)w + 0.5) * 0x1.0p-32; /* in (0, 1), exact */
+  return ((double)(w >> 1) + 0.5) * 0x1.0p-31; /* in (0, 1), exact */
 }
 
 /* Generic bonds over angles already widened to FP64 (ang[i]), for the
@@ -231,15 +248,15 @@ static long bonds_generic(int Lx, int Ly, int per_x, int per_y,
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long band = 0;
   for (uint64_t i = 0; i < n; ++i) {
-    uint32_t w[4];
-    philox_draw(seed, (uint32_t)i, (uint32_t)(i >> 32), t, ORC_DOM_BOND, w);
+    uint32_t w_right, w_down;
+    bond_words(seed, t, Lx, i, &w_right, &w_down);
     double ai = projection(ang[i], cphi, sphi);
     uint64_t j;
     right[i] = 0;
     if (right_of(Lx, Ly, per_x, i, &j)) {
       double aj = projection(ang[j], cphi, sphi);
       double p = bond_probability(ai, aj, beta);
-      double u = uniform_open(w[0]);
+      double u = uniform_open(w_right);
       right[i] = (ai * aj > 0.0) && (u < p);
       if (ai * aj > 0.0 && fabs(u - p) < 1e-12) ++band;
     }
@@ -247,7 +264,7 @@ static long bonds_generic(int Lx, int Ly, int per_x, int per_y,
     if (down_of(Lx, Ly, per_y, i, &j)) {
       double aj = projection(ang[j], cphi, sphi);
       double p = bond_probability(ai, aj, beta);
-      double u = uniform_open(w[1]);
+      double u = uniform_open(w_down);
       down[i] = (ai * aj > 0.0) && (u < p);
       if (ai * aj > 0.0 && fabs(u - p) < 1e-12) ++band;
     }
@@ -322,13 +339,12 @@ static void bond_up_generic(int Lx, int Ly, int per_x, int per_y,
                             const void *theta, double cphi, double sphi,
                             double beta, uint64_t seed, uint32_t t, int64_t i,
                             int dir, double *u, double *p) {
-  uint32_t w[4];
-  philox_draw(seed, (uint32_t)i, (uint32_t)((uint64_t)i >> 32), t,
-              ORC_DOM_BOND, w);
+  uint32_t w_right, w_down;
+  bond_words(seed, t, Lx, (uint64_t)i, &w_right, &w_down);
   uint64_t j;
   int ok = dir == 0 ? right_of(Lx, Ly, per_x, (uint64_t)i, &j)
                     : down_of(Lx, Ly, per_y, (uint64_t)i, &j);
-  *u = uniform_open(dir == 0 ? w[0] : w[1]);
+  *u = uniform_open(dir == 0 ? w_right : w_down);
   *p = 0.0;
   if (!ok) return;
   double ai = projection(angle(theta, (uint64_t)i), cphi, sphi);
@@ -456,10 +472,10 @@ long orc_label_uf(int Lx, int Ly, int per_x, int per_y, const uint8_t *right,
 /* ------------------------------------------------------------------------ */
 /* Step 4: flip.  Reflection about the axis: theta' = C - theta (mod 2 pi).  */
 /* ------------------------------------------------------------------------ */
-int orc_coin(uint64_t seed, uint32_t t, uint32_t root) {
-  uint32_t w[4];
-  philox_draw(seed, root, 0u, t, ORC_DOM_BOND, w);
-  return (int)(w[2] & 1u);
+int orc_coin(uint64_t seed, uint32_t t, int Lx, uint32_t root) {
+  uint32_t w_right, w_down;
+  bond_words(seed, t, Lx, root, &w_right, &w_down);
+  return (int)(w_right & 1u);
 }
 
 long orc_flip_f32(int Lx, int Ly, float *theta, const uint32_t *label,
@@ -467,7 +483,7 @@ long orc_flip_f32(int Lx, int Ly, float *theta, const uint32_t *label,
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long count = 0;
   for (uint64_t i = 0; i < n; ++i) {
-    int f = orc_coin(seed, t, label[i]);
+    int f = orc_coin(seed, t, Lx, label[i]);
     if (flipped) flipped[i] = (uint8_t)f;
     if (f) {
       theta[i] = wrap_f32(c32 - theta[i]);
@@ -482,7 +498,7 @@ long orc_flip_f16(int Lx, int Ly, uint16_t *theta_bits, const uint32_t *label,
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long count = 0;
   for (uint64_t i = 0; i < n; ++i) {
-    int f = orc_coin(seed, t, label[i]);
+    int f = orc_coin(seed, t, Lx, label[i]);
     if (flipped) flipped[i] = (uint8_t)f;
     if (f) {
       float v = wrap_f32(c32 - half_bits_to_float(theta_bits[i]));
@@ -499,7 +515,7 @@ long orc_flip_u16(int Lx, int Ly, uint16_t *q, const uint32_t *label,
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long count = 0;
   for (uint64_t i = 0; i < n; ++i) {
-    int f = orc_coin(seed, t, label[i]);
+    int f = orc_coin(seed, t, Lx, label[i]);
     if (flipped) flipped[i] = (uint8_t)f;
     if (f) {
       q[i] = (uint16_t)(((uint32_t)cq + 65536u - (uint32_t)q[i]) & 0xFFFFu);
@@ -753,13 +769,12 @@ static int bond_active(int Lx, int Ly, int per_x, int per_y, const double *ang,
   int ok = dir == 0 ? right_of(Lx, Ly, per_x, owner, &j)
                     : down_of(Lx, Ly, per_y, owner, &j);
   if (!ok) return 0;
-  uint32_t w[4];
-  philox_draw(seed, (uint32_t)owner, (uint32_t)(owner >> 32), t, ORC_DOM_BOND,
-              w);
+  uint32_t w_right, w_down;
+  bond_words(seed, t, Lx, owner, &w_right, &w_down);
   double ai = projection(ang[owner], cphi, sphi);
   double aj = projection(ang[j], cphi, sphi);
   double p = bond_probability(ai, aj, beta);
-  double u = uniform_open(dir == 0 ? w[0] : w[1]);
+  double u = uniform_open(dir == 0 ? w_right : w_down);
   return (ai * aj > 0.0) && (u < p);
 }
 

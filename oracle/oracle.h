@@ -18,11 +18,14 @@
  *   1. axis:  phi from Philox domain AXIS, r = (cos phi, sin phi),
  *             C = (pi + 2 phi) mod 2 pi, C32 = (float)C.
  *   2. bonds: a_i = s_i . r in FP64; right/down bond <ij> is active iff
- *             a_i a_j > 0 and u < 1 - exp(-2 beta a_i a_j), u from Philox
- *             domain BOND of site i (word 0 = right, word 1 = down).
+ *             a_i a_j > 0 and u < 1 - exp(-2 beta a_i a_j).  One Philox
+ *             draw of domain BOND serves the vertical pair of sites (x, 2m),
+ *             (x, 2m + 1) (counter word 0 = m Lx + x): row 2m takes words 0
+ *             (right) and 1 (down), row 2m + 1 words 2 and 3; a bond's u is
+ *             ((w >> 1) + 1/2) 2^-31 of its word w.
  *   3. labels: connected components of the active bonds; label = the minimum
  *             site index of the component (BFS; union-find as a second copy).
- *   4. flip:  a cluster flips iff word 2 of its root's BOND draw is odd;
+ *   4. flip:  a cluster flips iff bit 0 of its root's right-bond word is 1;
  *             a flipped angle becomes wrap(C32 - theta) in FP32, which is the
  *             reflection s' = s - 2 (s.r) r of Wolff's embedding.
  *   5. observables on the flipped configuration: energy, magnetisation and
@@ -147,7 +150,7 @@ long orc_flip_f16(int Lx, int Ly, uint16_t *theta_bits, const uint32_t *label,
 long orc_flip_u16(int Lx, int Ly, uint16_t *q, const uint32_t *label,
                   uint64_t seed, uint32_t t, uint16_t cq, uint8_t *flipped);
 /* coin of a root site: 1 = the cluster is reflected. */
-int orc_coin(uint64_t seed, uint32_t t, uint32_t root);
+int orc_coin(uint64_t seed, uint32_t t, int Lx, uint32_t root);
 
 /* Step 5: observables. */
 void orc_sums_f32(int Lx, int Ly, int per_x, int per_y, const float *theta,

@@ -66,7 +66,7 @@ def test_l65536_one_sweep_sampled(orc):
                 assert abs(u - p) <= eps, (int(i[k]), direction, u, p)
     # flips: each angle is 0 or C32 by the coin of its label
     c32 = orc.axis(seed, 0)[4]
-    coins = np.array([orc.coin(seed, 0, int(v)) for v in lab[:5000]])
+    coins = np.array([orc.coin(seed, 0, int(v), L) for v in lab[:5000]])
     np.testing.assert_array_equal(th[:5000], np.where(coins == 1, c32, np.float32(0.0)))
     # observables of a two-valued field
     r = rec[0]

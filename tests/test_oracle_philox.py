@@ -60,3 +60,24 @@ def test_philox_uniformity(orc):
     e = len(b) / 256.0
     chi2 = float(((h - e) ** 2 / e).sum())
     assert abs(chi2 - 255.0) < 5 * np.sqrt(2 * 255.0)
+
+
+def test_bond_words_pair_two_rows(orc):
+    """One BOND draw serves the vertical pair (x, 2m), (x, 2m + 1): counter
+    (m L + x, 0, t, BOND); row 2m reads words 0 (right) and 1 (down), row
+    2m + 1 words 2 and 3; u = ((w >> 1) + 1/2) 2^-31 and the coin is bit 0
+    of the right-bond word.  Checked against the Philox function pinned
+    above, for even and odd rows and for the last row of an odd L."""
+    seed, t = 0x0123456789ABCDEF, 5
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    for L in (8, 9):
+        theta = np.zeros(L * L, np.float32)
+        for i in range(L * L):
+            x, y = i % L, i // L
+            w = orc.philox(np.array([(y >> 1) * L + x, 0, t, 0], np.uint32), key)
+            wr, wd = (w[2], w[3]) if y & 1 else (w[0], w[1])
+            u_r, _ = orc.bond_up(theta, L, L, 1.0, seed, t, i, 0)
+            u_d, _ = orc.bond_up(theta, L, L, 1.0, seed, t, i, 1)
+            assert u_r == ((int(wr) >> 1) + 0.5) * 2.0 ** -31
+            assert u_d == ((int(wd) >> 1) + 0.5) * 2.0 ** -31
+            assert orc.coin(seed, t, i, L) == int(wr) & 1

@@ -110,7 +110,7 @@ def test_flip_is_vector_reflection(orc):
 
 def test_coin_is_fair(orc):
     n = 40000
-    flips = sum(orc.coin(77, t, r) for t in range(40) for r in range(n // 40))
+    flips = sum(orc.coin(77, t, r, 64) for t in range(40) for r in range(n // 40))
     assert abs(flips - n / 2) < 4 * math.sqrt(n / 4)
 
 
