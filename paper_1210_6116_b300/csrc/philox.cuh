@@ -8,14 +8,17 @@
 // constants between rounds.  One call yields four 32-bit words.
 //
 // Counter layout used throughout the library: (site, site >> 32, sweep,
-// domain); key = (seed low word, seed high word).
+// domain), except that the BOND domain counts pairs of rows (see below);
+// key = (seed low word, seed high word).
 #pragma once
 #include <cstdint>
 
 namespace xyk {
 
 enum : uint32_t {
-  kDomBond = 0,   // words 0/1: right/down bond uniforms, word 2: cluster coin
+  kDomBond = 0,   // one draw per vertical pair of sites (counter m L + x):
+                  // rows 2m / 2m+1 take words 0,1 / 2,3 as right, down; the
+                  // right-bond word's bit 0 is the site's cluster coin
   kDomAxis = 1,   // the random axis of a sweep
   kDomInit = 2,   // random initial angles (sweep word 0xffffffff)
 };

@@ -268,7 +268,7 @@ __device__ __forceinline__ Tile tile_geom(uint32_t L, uint32_t ntx, uint64_t ntx
 // bond decision
 // ---------------------------------------------------------------------------
 // FP64 rule, operation for operation: x = a_i a_j; active iff x > 0 and
-// (w + 1/2) 2^-32 < 1 - exp(-2 beta x).
+// ((w >> 1) + 1/2) 2^-31 < 1 - exp(-2 beta x).
 static __device__ __noinline__ bool bond_fp64(double th_i, double th_j, uint32_t word,
                                               double beta, double cphi, double sphi) {
   const double ai = project64(th_i, cphi, sphi);
@@ -276,8 +276,8 @@ static __device__ __noinline__ bool bond_fp64(double th_i, double th_j, uint32_t
   const double x = __dmul_rn(ai, aj);
   if (!(x > 0.0)) return false;
   const double p = __dsub_rn(1.0, exp(__dmul_rn(__dmul_rn(-2.0, beta), x)));
-  const double u = __dmul_rn(__dadd_rn(static_cast<double>(word), 0.5),
-                             0x1p-32);
+  const double u = __dmul_rn(__dadd_rn(static_cast<double>(word >> 1), 0.5),
+                             0x1p-31);
   return u < p;
 }
 
@@ -529,8 +529,12 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
       const float ac = project32(angle_f32<AT>(tc), cphi, sphi);
 
       // phase A: bonds and coins of every row of the band (rows are
-      // independent here, so their Philox chains overlap)
+      // independent here, so their Philox chains overlap).  One BOND draw
+      // serves the rows 2m and 2m + 1 of a column (counter m L + x): the
+      // band starts on an even row, so row k uses words 0 and 1 of the draw
+      // made at k for even k, words 2 and 3 of that draw for odd k.
       uint32_t Rws[B], Dws[B], Cws[B];
+      Words4 rn = {0u, 0u, 0u, 0u};
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         Rws[k] = Dws[k] = Cws[k] = 0u;
@@ -543,12 +547,14 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
         bool br = false, bd = false, cn = false;
         if (col_ok) {
           const uint32_t i = gy * L + g.x0 + lane;
-          const Words4 rn = philox4x32_10(i, 0u, t, kDomBond, d.key0, d.key1);
+          if ((k & 1) == 0)
+            rn = philox4x32_10((gy >> 1) * L + g.x0 + lane, 0u, t, kDomBond, d.key0, d.key1);
+          const uint32_t w_r = (k & 1) ? rn.w2 : rn.w0, w_d = (k & 1) ? rn.w3 : rn.w1;
           // uniforms from the top 23 bits without an int->float conversion:
           // 1.m - (1 - 2^-24) is exact and is the centre of the word's 2^-23
-          // bin, i.e. within 2^-24 of the FP64 uniform (w + 1/2) 2^-32
-          const float u0 = __uint_as_float(0x3F800000u | (rn.w0 >> 9)) - 0.99999994f;
-          const float u1 = __uint_as_float(0x3F800000u | (rn.w1 >> 9)) - 0.99999994f;
+          // bin, i.e. within 2^-24 of the FP64 uniform ((w >> 1) + 1/2) 2^-31
+          const float u0 = __uint_as_float(0x3F800000u | (w_r >> 9)) - 0.99999994f;
+          const float u1 = __uint_as_float(0x3F800000u | (w_d >> 9)) - 0.99999994f;
           const float xr = a[k] * a_r;
           const float xd = a[k] * a[k + 1];
           const float pr = xr > 0.0f ? 1.0f - __expf(-b2 * xr) : 0.0f;
@@ -563,14 +569,14 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
                 const float th_r = (static_cast<uint32_t>(lane) + 1u == g.w)
                                        ? load_angle(th, static_cast<uint64_t>(gy) * L + g.xh)
                                        : load_angle(th, static_cast<uint64_t>(i) + 1u);
-                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(th_r), rn.w0,
+                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(th_r), w_r,
                                          st->beta, st->cphi, st->sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != br) atomicAdd(&st->n_fp32_wrong, 1ull);
                 br = e;
               }
               if (amb_d) {
-                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(tv[k + 1]), rn.w1,
+                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(tv[k + 1]), w_d,
                                          st->beta, st->cphi, st->sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != bd) atomicAdd(&st->n_fp32_wrong, 1ull);
@@ -578,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
               }
             }
           }
-          cn = (rn.w2 & 1u) != 0u;
+          cn = (w_r & 1u) != 0u;  // the coin: bit 0 of the right-bond word
         }
         Rws[k] = __ballot_sync(0xFFFFFFFFu, br);
         Dws[k] = __ballot_sync(0xFFFFFFFFu, bd);
