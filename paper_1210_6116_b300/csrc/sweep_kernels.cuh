@@ -461,8 +461,8 @@ constexpr size_t bond_label_smem() {
 // K1: projection + bonds + coins + tile labels
 // ---------------------------------------------------------------------------
 // CTAs per SM: the whole-tile FP32-threshold sweep kernel fits 6 (40
-// registers, no spills; at L = 4096 151 -> 139 us against 4); the general
-// ones keep 4, where more would spill.
+// registers, 8 bytes spilled; at L = 4096 it beats 5 CTAs/SM by 4.5 us and
+// 4 by ~12 us); the general ones keep 4, where more would spill.
 template <int TY, bool EXACT, bool FROM_PLANES, bool FULL>
 constexpr int k1_min_blocks() {
   return (FULL && !EXACT && !FROM_PLANES && TY <= 64) ? 6 : 4;
