@@ -1025,13 +1025,9 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     for (int k = 0; k < NV; ++k) {
       const int t = static_cast<int>(acc[k] - rows * 0x40400000u);  // |sum| <= B 2^22
       if constexpr (B <= 8) {
-        // a warp's sum stays within 32 x 8 x 2^22 = 2^30: reduce in 32 bits
-        int w = t;
-        if (k < nv) {
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xFFFFFFFFu, w, off);
-        }
-        v[k] = w;
+        // a warp's sum stays within 32 x 8 x 2^22 = 2^30: one 32-bit warp
+        // reduction instruction (exact integer sum)
+        v[k] = (k < nv) ? __reduce_add_sync(0xFFFFFFFFu, t) : t;
       } else {
         v[k] = t;
         if (k < nv) {
