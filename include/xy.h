@@ -200,6 +200,13 @@ xy_status xy_destroy(xy_lattice *h);
  * otherwise (every u16 value is valid). */
 xy_status xy_get_angles(xy_lattice *h, void *host_dst);
 xy_status xy_set_angles(xy_lattice *h, const void *host_src);
+/* Spin vectors s_i = (cos theta_i, sin theta_i) of the current angles (the
+ * O(2) spins of Eq. (1)), N floats each, row-major, evaluated on the device
+ * by the same cos/sin routine the observable sums of xy_measure use
+ * (absolute error <= 1e-7).  Either output may be NULL.  Synchronising;
+ * allocates a device buffer of at most 32 MiB for the call and frees it
+ * before returning. */
+xy_status xy_get_spins(xy_lattice *h, float *host_cos, float *host_sin);
 /* Bonds of the last sweep as N bytes each (1 = active): right[i] is the bond
  * (x, y)-(x+1 mod L, y), down[i] the bond (x, y)-(x, y+1 mod L). */
 xy_status xy_get_bonds(xy_lattice *h, uint8_t *host_right,

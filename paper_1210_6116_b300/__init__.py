@@ -51,7 +51,7 @@ STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "X
 EXPORTS = (
     "xy_last_error", "xy_workspace_size", "xy_init", "xy_sweep", "xy_pcc_step",
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
-    "xy_get_bonds", "xy_get_labels", "xy_get_sites", "xy_label_bonds", "xy_get_band_stats",
+    "xy_get_bonds", "xy_get_labels", "xy_get_sites", "xy_get_spins", "xy_label_bonds", "xy_get_band_stats",
     "xy_save", "xy_load", "xy_run_host", "xy_run_host_async", "xy_sync", "xy_profile",
     "xy_profile_read", "xy_label_bonds_static",
     "xy_engine_workspace_size", "xy_engine_create", "xy_engine_admit", "xy_engine_retire",
@@ -125,6 +125,7 @@ def load_library() -> ctypes.CDLL:
         "xy_get_bonds": (I, [P, P, P]),
         "xy_get_labels": (I, [P, P]),
         "xy_get_sites": (I, [P, P, ctypes.c_uint32, P, P, P]),
+        "xy_get_spins": (I, [P, P, P]),
         "xy_label_bonds": (I, [P, P, P, P]),
         "xy_get_band_stats": (I, [P, P, P]),
         "xy_save": (I, [P, P, P]),
@@ -281,6 +282,14 @@ class Lattice:
         a = np.ascontiguousarray(a, dtype=self.np_dtype)
         assert a.size == self.n
         _check(load_library().xy_set_angles(self.handle, _ptr(a)))
+
+    def get_spins(self):
+        """(cos theta, sin theta) of the current angles, float32 arrays of N,
+        from the observables' device cos/sin routine."""
+        c = np.zeros(self.n, np.float32)
+        s = np.zeros(self.n, np.float32)
+        _check(load_library().xy_get_spins(self.handle, _ptr(c), _ptr(s)))
+        return c, s
 
     def get_bonds(self):
         r = np.zeros(self.n, np.uint8)

@@ -192,10 +192,46 @@ __device__ __forceinline__ float reflect<uint16_t>(float raw, float c) {
   const uint32_t q = static_cast<uint32_t>(raw), cq = static_cast<uint32_t>(c);
   return static_cast<float>((cq + 65536u - q) & 0xFFFFu);
 }
-// sin and cos of the angle for the observables (accurate, not the SFU)
+// sin and cos of an angle x with |x| <= 8 (stored angles lie in [0, 2 pi)),
+// for the observables.  Cody-Waite reduction by pi/2 (W. J. Cody and
+// W. Waite, Software Manual for the Elementary Functions, 1980): q is the
+// integer nearest x 2/pi, r = x - q P1 - q P2 with P1 the float nearest pi/2
+// and P2 the float nearest pi/2 - P1.  The first FMA is exact (q <= 5: the
+// difference is a multiple of 2^-24 below 1 in magnitude), the second rounds
+// once (<= 3e-8), and pi/2 - P1 - P2 = -1.8e-15 is negligible.  Then the
+// Taylor polynomials of sin to r^9 and of cos to r^10 on |r| <= pi/4
+// (truncation <= 1.8e-9), evaluated by Horner with FMAs, and the quadrant
+// q mod 4 by swapping and sign flips.  Absolute error <= 1e-7 for both (the
+// tests measure it against FP64); the SFU's __sincosf (~3.6e-7) is not
+// accurate enough for the observable tolerances.
+__device__ __forceinline__ void sincos_cw(float x, float *s, float *c) {
+  constexpr float kTwoOverPi = 0x1.45f306p-1f;  // float nearest 2/pi
+  constexpr float kP1 = 0x1.921fb6p+0f;         // float nearest pi/2
+  constexpr float kP2 = -0x1.777a5cp-25f;       // float nearest pi/2 - kP1
+  constexpr float kRound = 0x1.8p23f;           // 1.5 2^23: adds round to integers
+  const float t = fmaf(x, kTwoOverPi, kRound);   // kRound + q
+  const float q = t - kRound;                    // exact
+  const uint32_t iq = __float_as_uint(t);        // low bits: q mod 4
+  float r = fmaf(-q, kP1, x);
+  r = fmaf(-q, kP2, r);
+  const float r2 = r * r;
+  float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(ps, r2, 1.0f / 120.0f);
+  ps = fmaf(ps, r2, -1.0f / 6.0f);
+  const float sr = fmaf(ps * r2, r, r);
+  float pc = fmaf(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(pc, r2, -1.0f / 720.0f);
+  pc = fmaf(pc, r2, 1.0f / 24.0f);
+  pc = fmaf(pc, r2, -0.5f);
+  const float cr = fmaf(pc, r2, 1.0f);
+  // (sin, cos)(r + q pi/2) = (sr, cr), (cr, -sr), (-sr, -cr), (-cr, sr)
+  const bool odd = (iq & 1u) != 0u;
+  *s = __uint_as_float(__float_as_uint(odd ? cr : sr) ^ ((iq & 2u) << 30));
+  *c = __uint_as_float(__float_as_uint(odd ? sr : cr) ^ (((iq + 1u) & 2u) << 30));
+}
 template <typename AT>
 __device__ __forceinline__ void sin_cos(float raw, float *s, float *c) {
-  sincosf(raw, s, c);
+  sincos_cw(raw, s, c);
 }
 template <>
 __device__ __forceinline__ void sin_cos<uint16_t>(float raw, float *s, float *c) {

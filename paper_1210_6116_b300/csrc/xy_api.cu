@@ -254,6 +254,20 @@ __global__ void k_gather_sites(LatDesc d, uint32_t TY, const uint64_t *__restric
                                       (((d.dplane[w] >> (x & 31u)) & 1u) << 1));
 }
 
+// cos and sin of the angles i0 .. i0 + n - 1 with the observables' routine
+template <typename AT>
+__global__ void k_spins(LatDesc d, uint32_t cur, uint64_t i0, uint64_t n, float *cs,
+                        float *sn) {
+  const AT *th = static_cast<const AT *>(d.theta[cur]);
+  for (uint64_t k = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+       k += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    float s, c;
+    sin_cos<AT>(load_angle(th, i0 + k), &s, &c);
+    cs[k] = c;
+    sn[k] = s;
+  }
+}
+
 extern "C" {
 
 const char *xy_last_error(void) { return g_err; }
@@ -492,6 +506,36 @@ xy_status xy_get_angles(xy_lattice *h, void *host_dst) {
   XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
   const size_t bytes = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
   XY_CUDA(cudaMemcpy(host_dst, h->desc.theta[s.cur], bytes, cudaMemcpyDeviceToHost));
+  return XY_OK;
+}
+
+xy_status xy_get_spins(xy_lattice *h, float *host_cos, float *host_sin) {
+  if (!h) return fail(XY_EINVAL, "NULL lattice");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  DevState st;
+  XY_CUDA(cudaMemcpy(&st, h->d_state, sizeof(st), cudaMemcpyDeviceToHost));
+  const uint64_t n = static_cast<uint64_t>(h->lo.L) * h->lo.L;
+  const uint64_t chunk = std::min<uint64_t>(n, 1ull << 22);  // 2 x 16 MiB
+  float *buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, chunk * 2 * sizeof(float));
+  for (uint64_t i0 = 0; e == cudaSuccess && i0 < n; i0 += chunk) {
+    const uint64_t m = std::min(chunk, n - i0);
+    const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((m + 255) / 256, static_cast<uint64_t>(h->sm_count) * 16));
+    if (h->cfg.angle_dtype == XY_F32)
+      k_spins<float><<<blocks, 256, 0, h->stream>>>(h->desc, st.cur, i0, m, buf, buf + chunk);
+    else if (h->cfg.angle_dtype == XY_F16)
+      k_spins<__half><<<blocks, 256, 0, h->stream>>>(h->desc, st.cur, i0, m, buf, buf + chunk);
+    else
+      k_spins<uint16_t><<<blocks, 256, 0, h->stream>>>(h->desc, st.cur, i0, m, buf, buf + chunk);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && host_cos)
+      e = cudaMemcpy(host_cos + i0, buf, m * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_sin)
+      e = cudaMemcpy(host_sin + i0, buf + chunk, m * sizeof(float), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(XY_ECUDA, "xy_get_spins: %s", cudaGetErrorString(e));
   return XY_OK;
 }
 

@@ -2,7 +2,9 @@
 
 Tolerances, derived from the arithmetic of the observable kernel.  Each site
 term is evaluated in FP32 from the stored angles: cos/sin of an angle with
-sincosf (<= 2 ulp, i.e. <= 1.2e-7 absolute for values in [-1, 1]), and a link
+the kernel's own routine (Cody-Waite reduction and Taylor polynomials,
+<= 1e-7 absolute, measured in test_gpu_spins; the bounds below allow
+1.2e-7), and a link
 term cos(ti - tj) = ci cj + si sj (or si cj - ci sj) with error
 <= 1.2e-7 * (|ci| + |cj| + |si| + |sj|) + 1.2e-7 <= 4.6e-7.  Every term is then
 rounded to a 2^-22 grid (<= 2^-23 = 1.2e-7) and summed exactly in integers.
