@@ -928,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     const bool vc = static_cast<uint32_t>(lane) < nb;  // column xh, row r0+lane
     const uint64_t ic = static_cast<uint64_t>(g.y0 + r0 + lane) * L + g.xh;
 
-    // round 1: labels and angles of rows r0 .. r0+nb and of column xh
+    // step 1: labels and angles of rows r0 .. r0+nb and of column xh
     uint32_t l[B + 1];
     float t[B + 1];
 #pragma unroll
@@ -948,7 +948,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       lc = __ldcg(lab + ic);
       if (!LABELS_ONLY) tc = load_angle(thin, ic);
     }
-    // round 2: the tile root's entry
+    // step 2: the tile root's entry
     uint32_t p[B + 1];
 #pragma unroll
     for (int k = 0; k <= B; ++k)
@@ -969,7 +969,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       }
     }
     if (LABELS_ONLY) continue;
-    // round 4: which sites reflect.  SW: the coin of the site's root.
+    // step 3: which sites reflect.  SW: the coin of the site's root.
     // Wolff: the sites of the seed site's cluster, whose root is the entry's
     // entry of the seed like any other site's (whether or not this kernel
     // has already rewritten those entries: both reads give the root)

@@ -11,7 +11,7 @@ rounded to a 2^-22 grid (<= 2^-23 = 1.2e-7) and summed exactly in integers.
 Per site, a link sum (e_x, s_x, e_y, s_y) is therefore within
 EPS_LINK = 6e-7 of the oracle's FP64 sum / N, a site sum (m_x, m_y) within
 EPS_SITE = 2.4e-7, and E/site (two links per site) within 2 EPS_LINK.
-The north star's "1e-6 relative" holds on top of these wherever the value is
+The 1e-6 relative target for the observables holds on top of these wherever the value is
 O(1) (E/site ~ -1.4, e_x ~ 0.7): the test takes max(1e-6 |value|, bound).
 M^2 = mx^2 + my^2 and Upsilon = e_x - beta N s_x^2 inherit the bounds by
 error propagation.
