@@ -499,12 +499,14 @@ constexpr size_t bond_label_smem() {
 // ---------------------------------------------------------------------------
 // K1: projection + bonds + coins + tile labels
 // ---------------------------------------------------------------------------
-// CTAs per SM: the whole-tile FP32-threshold sweep kernel fits 6 (40
-// registers, 8 bytes spilled; at L = 4096 it beats 5 CTAs/SM by 4.5 us and
-// 4 by ~12 us); the general ones keep 4, where more would spill.
+// CTAs per SM: the whole-tile sweep kernels fit 6 (40 registers).  With
+// FP32 thresholds 8 bytes spill, and 6 beats 5 CTAs/SM by 4.5 us and 4 by
+// ~12 us at L = 4096.  In exact mode the spills (84 bytes) sit mostly on the
+// rare FP64 path, and 6 CTAs/SM still beat 4 by 12.8 us per sweep.  The
+// general instantiations keep 4.
 template <int TY, bool EXACT, bool FROM_PLANES, bool FULL>
 constexpr int k1_min_blocks() {
-  return (FULL && !EXACT && !FROM_PLANES && TY <= 64) ? 6 : 4;
+  return (FULL && !FROM_PLANES && TY <= 64) ? 6 : 4;
 }
 
 template <int TY, typename AT, bool EXACT, bool FROM_PLANES, bool FULL = false>
