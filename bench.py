@@ -32,22 +32,27 @@ sys.path.insert(0, str(ROOT))
 METRIC = "spin updates/ns per SW sweep (L=4096, 65536) & %HBM roofline; batched sweeps/s, p50/p99"
 UNIT = "spin updates/ns"
 
-# Algorithmic bytes per site of each kernel (FP32 angles): what the step must
-# move at minimum for that kernel's share of the work.
 PROFILE_EVERY = 16  # kernel-timing stride inside timed regions
-KERNEL_BYTES_PER_SITE = {
-    # angles in, tile labels out, bond planes, coin bits, tile edge table
-    "bond_label": 4.0 + 4.0 + 0.25 + 0.125 + 0.375,
-    # labels in, angles in and out (canonical labels are stored only by the
-    # last sweep of a call)
-    "flip_measure": 4.0 + 4.0 + 4.0,
-}
-# Whole-sweep byte models (per site): the method's minimum (angles read and
-# written once, one label per site written once and read once, bond and
-# coin bits), and the pipeline this library runs (K1, merge and compress
-# at ~0.5 B/site each, K4).
-M_CANON = 4.0 + 4.0 + 4.0 + 4.0 + 0.375
-M_BUILT = KERNEL_BYTES_PER_SITE["bond_label"] + 0.5 + 0.5 + KERNEL_BYTES_PER_SITE["flip_measure"]
+
+# Byte models of a sweep, per site, FP32 angles (the hot-path scope's
+# measurement section):
+#   M_alg   the method's minimum: angles read in the bond pass (4), read and
+#           written in the flip pass after global connectivity (4 + 4), bond
+#           bits written and read (0.25 + 0.25)                    = 12.5
+#   M_canon M_alg + one uint32 canonical label written once        = 16.5
+# Each kernel's share of M_alg (the roofline of the dominant kernel is taken
+# against its share): the bond + label kernel reads the angles and writes the
+# bond bits, the flip kernel reads and writes the angles and (in the model)
+# reads the bond bits back.
+M_ALG = 4.0 + 4.0 + 4.0 + 0.25 + 0.25
+M_CANON = M_ALG + 4.0
+ALG_SHARE = {"bond_label": 4.0 + 0.25, "flip_measure": 4.0 + 4.0 + 0.25}
+# Bytes the built pipeline moves per site (its own intermediates included):
+# bond + label kernel: angles in, tile labels out, bond planes, coin bits,
+# tile edge table; merge and compress ~0.5 each (upper figures); flip kernel:
+# labels in, angles in and out.
+BUILT_SHARE = {"bond_label": 4.0 + 4.0 + 0.25 + 0.125 + 0.375, "flip_measure": 12.0}
+M_BUILT = BUILT_SHARE["bond_label"] + 0.5 + 0.5 + BUILT_SHARE["flip_measure"]
 
 
 def _sm_max_mhz():
@@ -66,52 +71,94 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms from before
+    the warm-up until after the timed region.  The GPU is named by its UUID
+    (the process's device 0 need not be nvidia-smi's index 0).  The summary
+    takes the samples inside the timed region, or, when the region is shorter
+    than the sampling interval, the samples nearest to it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int):
-        self.gpu = gpu
+    def __init__(self, device: int):
+        self.device = device
         self.proc = None
+        self.samples = []  # (monotonic time, fields)
+        self.window = None
+        self.error = None
 
-    def __enter__(self):
+    def start(self):
+        import threading
+
+        import torch
+
         try:
+            gpu = "GPU-" + str(torch.cuda.get_device_properties(self.device).uuid)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", gpu, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+                stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+        except (OSError, AssertionError, RuntimeError) as e:
+            self.error = f"nvidia-smi not started: {e}"
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    self.samples.append((time.monotonic(), f))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        t0 = time.monotonic()
+        while not self.samples and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.02)
         return self
 
-    def __exit__(self, *a):
-        self.samples = []
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
+
+    def stop(self):
         if self.proc is None:
             return
+        time.sleep(0.25)  # one more sample after the timed region
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            _, err = self.proc.communicate(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        for line in out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
-                self.samples.append(f)
+            _, err = self.proc.communicate()
+        if not self.samples:
+            self.error = "nvidia-smi gave no samples: " + (err or "").strip()[:200]
 
     def summary(self):
-        if not getattr(self, "samples", None):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "error": self.error or "no samples"}
+        t0, t1 = self.window or (self.samples[0][0], self.samples[-1][0])
+        inside = [f for t, f in self.samples if t0 <= t <= t1]
+        how = "samples inside the timed region"
+        if not inside:
+            near = sorted(self.samples, key=lambda s: min(abs(s[0] - t0), abs(s[0] - t1)))[:2]
+            inside = [f for _, f in near]
+            how = ("timed region shorter than the 200 ms sampling interval: "
+                   "the samples nearest to it")
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [v for v in (num(f[1]) for f in inside) if v is not None]
+        mx = [v for v in (num(f[2]) for f in inside) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4)
-                          if s[5 + k].lower().startswith("active")})
+        reasons = sorted({names[k] for f in inside for k in range(4)
+                          if f[5 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "samples": len(inside), "how": how}
 
 
 def _dist():
@@ -154,6 +201,7 @@ def run_ours(args):
         pg.barrier()
     L, beta = args.L, args.beta
     N = L * L
+    clk = ClockSampler(local).start()
     lat = xy.Lattice(L, beta, seed=1000 + rank, tile_y=args.tile_y, exact=bool(args.exact))
     stream = lat.stream
     lat.sweep(args.warmup)
@@ -168,15 +216,16 @@ def run_ours(args):
     # bracketing a sweep's kernels cost it ~12 us, so timing every sweep
     # would understate the rate by ~4 %
     lat.profile(True, every=PROFILE_EVERY)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        done = 0
-        while done < args.steps:
-            n = min(1024, args.steps - done)
-            lat.sweep(n)
-            done += n
-        ev1.record(stream)
-        torch.cuda.synchronize()
+    t_start = time.monotonic()
+    ev0.record(stream)
+    done = 0
+    while done < args.steps:
+        n = min(1024, args.steps - done)
+        lat.sweep(n)
+        done += n
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark(t_start, time.monotonic())
     if pg:
         pg.barrier()
     ms = ev0.elapsed_time(ev1)
@@ -185,38 +234,20 @@ def run_ours(args):
     recs = lat.measure()
     value, t_sec = aggregate(pg, ws, N, args.steps, ms / 1e3, device="cuda")
     ms_per_step = t_sec * 1e3 / args.steps
-    launches = 5 * args.steps + math.ceil(args.steps / 1024)
+    launches = xy.LAUNCHES_PER_SWEEP * args.steps + math.ceil(args.steps / 1024)
 
     out = None
     if rank == 0:
         peak, peak_kind = _peaks()
-        # dominant kernel
-        dom = max(KERNEL_BYTES_PER_SITE, key=lambda k: kt[k][0])
+        # dominant kernel, against its share of the method's bytes (M_alg)
+        dom = max(ALG_SHARE, key=lambda k: kt[k][0])
         dms = kt[dom][0] / kt[dom][1]
-        dbytes = KERNEL_BYTES_PER_SITE[dom] * N
-        achieved = dbytes / (dms * 1e-3) / 1e9
-        kernels = {k: {"ms_per_launch": round(v[0] / v[1], 5), "share": round(v[0] / sum(x[0] for x in kt.values()), 4)}
-                   for k, v in kt.items()}
-        traffic = None
-        alu = None
-        tfile = ROOT / "profiles" / "traffic.json"
-        if tfile.exists():
-            import hashlib
-            tj = json.loads(tfile.read_text())
-            src = ROOT / "paper_1210_6116_b300" / "csrc" / "sweep_kernels.cuh"
-            same = hashlib.sha256(src.read_bytes()).hexdigest()[:16] == tj.get("kernels_source_sha256_16")
-            if same and tj.get("kernel") == dom and tj.get("L") == L:
-                traffic = tj.get("bytes_per_launch")
-                if tj.get("thread_inst_per_launch"):
-                    # instruction issue ceiling: 148 SMs x 4 schedulers x 32 lanes x SM clock
-                    peak_ti = 148 * 4 * 32 * _sm_max_mhz() * 1e6 / 1e12
-                    ach_ti = tj["thread_inst_per_launch"] / (dms * 1e-3) / 1e12
-                    alu = {"bound": "alu", "kernel": dom, "achieved": round(ach_ti, 2),
-                           "peak": round(peak_ti, 2), "unit": "T thread-instructions/s",
-                           "frac": round(ach_ti / peak_ti, 4),
-                           "thread_inst_per_launch": tj["thread_inst_per_launch"],
-                           "how": "executed instructions from the ncu capture in profiles/, "
-                                  "duration from this run's CUDA events"}
+        achieved = ALG_SHARE[dom] * N / (dms * 1e-3) / 1e9
+        achieved_built = BUILT_SHARE[dom] * N / (dms * 1e-3) / 1e9
+        tot = sum(x[0] for x in kt.values())
+        kernels = {k: {"ms_per_launch": round(v[0] / v[1], 5), "share": round(v[0] / tot, 4)}
+                   for k, v in kt.items() if v[1]}
+        traffic, alu = _traffic_and_alu(dom, L, dms)
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -224,23 +255,32 @@ def run_ours(args):
             "dtype": "f32", "data": "synthetic",
             "config": bench_config(args, ws),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
-                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "bytes_per_site": KERNEL_BYTES_PER_SITE[dom]},
+                         "peak": peak, "peak_kind": f"{peak_kind} (burst copy; of measured)",
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "bytes_per_site": ALG_SHARE[dom],
+                         "model": "the kernel's share of M_alg (angles in, bond bits out)",
+                         "achieved_built_bytes": round(achieved_built, 1),
+                         "frac_built_bytes": round(achieved_built / peak, 4),
+                         "built_bytes_per_site": BUILT_SHARE[dom]},
             "roofline_alu": alu,
-            "sweep_roofline": {"model_canon_B_per_site": M_CANON, "model_built_B_per_site": M_BUILT,
-                               "frac_canon": round(value * M_CANON / peak, 4),
-                               "frac_built": round(value * M_BUILT / peak, 4)},
+            "sweep_roofline": {"M_alg_B_per_site": M_ALG, "M_canon_B_per_site": M_CANON,
+                               "M_built_B_per_site": M_BUILT,
+                               "frac_alg": round(value / ws * M_ALG / peak, 4),
+                               "frac_canon": round(value / ws * M_CANON / peak, 4),
+                               "frac_built": round(value / ws * M_BUILT / peak, 4)},
             "kernels": kernels,
             "kernel_timing": f"CUDA events around the kernels of every {PROFILE_EVERY}th sweep of the timed region",
             "gpu_launches": launches,
-            "clocks": clk.summary(),
             "last_energy_per_site": float(recs[-1]["energy_per_site"]) if len(recs) else None,
         }
     # end to end through the C ABI with pinned host buffers
     e2e = run_e2e(lat, args, N)
+    clk.stop()
     if rank == 0:
+        out["clocks"] = clk.summary()
         out["e2e"] = e2e
+        if args.protocol:
+            out["cfg1_protocol"] = run_cfg1_protocol(xy, args)
         if args.exact_report:
             out["exact_mode"] = exact_report(xy, L, beta, args)
             out["storage"] = storage_report(xy, L, beta, args)
@@ -261,6 +301,67 @@ def run_ours(args):
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def _traffic_and_alu(dom: str, L: int, dms: float):
+    """DRAM bytes per launch of the dominant kernel (ncu, profiles/traffic.json)
+    and its executed instructions against the issue ceiling, while the kernel
+    source is the one the capture was taken from (else null)."""
+    import hashlib
+
+    tfile = ROOT / "profiles" / "traffic.json"
+    if not tfile.exists():
+        return None, None
+    tj = json.loads(tfile.read_text())
+    src = ROOT / "paper_1210_6116_b300" / "csrc" / "sweep_kernels.cuh"
+    same = hashlib.sha256(src.read_bytes()).hexdigest()[:16] == tj.get("kernels_source_sha256_16")
+    if not (same and tj.get("kernel") == dom and tj.get("L") == L):
+        return None, None
+    traffic = tj.get("bytes_per_launch")
+    alu = None
+    if tj.get("thread_inst_per_launch"):
+        # instruction issue ceiling: 148 SMs x 4 schedulers x 32 lanes x SM clock
+        peak_ti = 148 * 4 * 32 * _sm_max_mhz() * 1e6 / 1e12
+        ach_ti = tj["thread_inst_per_launch"] / (dms * 1e-3) / 1e12
+        alu = {"bound": "alu", "kernel": dom, "achieved": round(ach_ti, 2),
+               "peak": round(peak_ti, 2), "unit": "T thread-instructions/s",
+               "frac": round(ach_ti / peak_ti, 4),
+               "thread_inst_per_launch": tj["thread_inst_per_launch"],
+               "how": "executed instructions from the ncu capture in profiles/, "
+                      "duration from this run's CUDA events"}
+    return traffic, alu
+
+
+def run_cfg1_protocol(xy, args):
+    """The L = 4096 workload's own protocol: beta in {1.10, 1.12, 1.14}, each
+    on a fresh lattice (seed 1000 + k) thermalised by 10^3 sweeps, then five
+    windows of 10^3 sweeps timed with CUDA events; the rate is the median of
+    the windows."""
+    import torch
+
+    L, N = args.L, args.L * args.L
+    out = {"L": L, "thermalisation_sweeps": args.therm, "windows": args.windows,
+           "window_sweeps": args.window_sweeps, "thresholds": "fp64-exact" if args.exact else "fp32"}
+    per_beta = {}
+    for k, beta in enumerate((1.10, 1.12, 1.14)):
+        lat = xy.Lattice(L, beta, seed=1000 + k, tile_y=args.tile_y, exact=bool(args.exact))
+        lat.sweep(args.therm)
+        lat.measure(max_records=0)
+        rates = []
+        for _ in range(args.windows):
+            t = _event_time(lambda: lat.sweep(args.window_sweeps), lat.stream)
+            rates.append(N * args.window_sweeps / (t * 1e9))
+        recs = lat.measure()
+        per_beta[f"{beta:.2f}"] = {
+            "median_updates_per_ns": round(statistics.median(rates), 3),
+            "windows_updates_per_ns": [round(r, 3) for r in rates],
+            "mean_energy_per_site": round(float(recs["energy_per_site"].mean()), 6),
+            "mean_beta_upsilon": round(float((recs["beta"] * recs["upsilon"]).mean()), 5)}
+        lat.close()
+    out["per_beta"] = per_beta
+    out["median_updates_per_ns"] = round(statistics.median(
+        v["median_updates_per_ns"] for v in per_beta.values()), 3)
+    return out
 
 
 def run_e2e(lat, args, N):
@@ -390,6 +491,10 @@ def wolff_report(xy, L, beta, args):
 
 
 def run_big(xy, args):
+    """L = 65536 (2^32 spins, the paper's largest lattice): 100 sweeps timed
+    from the ordered start at beta = 1.1199 (the workload as specified), then,
+    after --big-therm more sweeps, another timed window on the thermalised
+    lattice, whose clusters have the equilibrium structure."""
     import torch
 
     L = 65536
@@ -400,31 +505,35 @@ def run_big(xy, args):
     if cfg_bytes > 0.9 * free:
         return {"skipped": f"needs {cfg_bytes/1e9:.1f} GB, {free/1e9:.1f} GB free"}
     lat = xy.Lattice(L, 1.1199, seed=2, start="ordered", tile_y=args.tile_y, exact=bool(args.exact))
-    lat.sweep(2)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    n = args.big_steps
-    lat.profile(True)
-    e0.record(lat.stream)
-    lat.sweep(n)
-    e1.record(lat.stream)
-    torch.cuda.synchronize()
-    kt = lat.profile_read()
-    lat.profile(False)
-    ms = e0.elapsed_time(e1) / n
-    recs = lat.measure()
     peak, _ = _peaks()
-    v = L * L / (ms * 1e6)
-    out = {"value": round(v, 3), "unit": UNIT, "ms_per_step": round(ms, 4), "steps": n,
-           "beta": 1.1199, "start": "ordered",
-           "frac_canon": round(v * M_CANON / peak, 4), "frac_built": round(v * M_BUILT / peak, 4),
-           "bytes_per_sweep_model_canon": M_CANON * L * L,
-           "kernels_ms": {k: round(val[0] / val[1], 4) for k, val in kt.items()},
-           "last_energy_per_site": float(recs[-1]["energy_per_site"])}
+
+    def window(n):
+        lat.profile(True, every=max(1, n // 10))
+        t = _event_time(lambda: lat.sweep(n), lat.stream)
+        kt = lat.profile_read()
+        lat.profile(False)
+        recs = lat.measure()
+        v = L * L * n / (t * 1e9)
+        return {"value": round(v, 3), "unit": UNIT, "ms_per_step": round(t * 1e3 / n, 4), "steps": n,
+                "frac_alg": round(v * M_ALG / peak, 4), "frac_canon": round(v * M_CANON / peak, 4),
+                "frac_built": round(v * M_BUILT / peak, 4),
+                "kernels_ms": {k: round(val[0] / val[1], 4) for k, val in kt.items() if val[1]},
+                "mean_energy_per_site": round(float(recs["energy_per_site"].mean()), 6),
+                "last_m2": float(recs[-1]["m2"])}
+
+    out = {"L": L, "beta": 1.1199, "start": "ordered", "seed": 2,
+           "workspace_GB": round(cfg_bytes / 1e9, 2),
+           "bytes_per_sweep_M_alg": M_ALG * L * L, "bytes_per_sweep_M_canon": M_CANON * L * L}
+    out["from_ordered_start"] = window(args.big_steps)
+    if args.big_therm > 0:
+        lat.sweep(args.big_therm)
+        lat.measure(max_records=0)
+        out["thermalised"] = window(args.big_steps)
+        out["thermalised"]["after_sweeps"] = args.big_steps + args.big_therm
     lat.close()
     del lat
     torch.cuda.empty_cache()
+    out["value"] = out["from_ordered_start"]["value"]
     return out
 
 
@@ -545,63 +654,77 @@ def run_precision(xy, args):
 
 
 def cpu_baseline(args):
-    """The oracle as it stands, single-threaded, on a bounded sample."""
-    import numpy as np
-
+    """The oracle as it stands on the host cores: its OpenMP build on every
+    core (bonds, flip and observables parallel, labeling sequential) over
+    --cpu-sweeps sweeps of the benchmark lattice, and beside it the plain
+    single-threaded oracle over one sweep."""
     import oracle
 
     oracle.build()
     L = args.L
+    cores = os.cpu_count() or 1
+    threads = oracle.omp_threads(cores)
     th = oracle.init_angles(L, 1000, 0)
     n = args.cpu_sweeps
     t0 = time.perf_counter()
-    oracle.sw_run(th, L, L, args.beta, 1000, 0, n)
+    oracle.sw_run(th, L, L, args.beta, 1000, 0, n, omp=True)
     dt = time.perf_counter() - t0
-    return {"value": round(n * L * L / (dt * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} sweeps of the L={L} lattice (beta={args.beta}), {dt:.1f} s",
-            "host_cores_available": os.cpu_count()}
+    th1 = oracle.init_angles(L, 1000, 0)
+    t1 = time.perf_counter()
+    oracle.sw_run(th1, L, L, args.beta, 1000, 0, 1)
+    dt1 = time.perf_counter() - t1
+    return {"value": round(n * L * L / (dt * 1e9), 6), "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{n} sweeps of the L={L} lattice (beta={args.beta}) from the random start, "
+                      f"{dt:.1f} s, OpenMP build on {threads} threads (labeling sequential)",
+            "single_thread": {"value": round(L * L / (dt1 * 1e9), 6), "unit": UNIT, "cores": 1,
+                              "sample": f"1 sweep of the same lattice, {dt1:.1f} s"},
+            "host_cores_available": cores}
 
 
 def bench_config(args, ws: int) -> dict:
-    """The workload both arms report (the reference arm times a bounded
-    sample of it, described in its cpu_baseline)."""
+    """The workload both arms report and time (the reference arm runs it on
+    the host cores, see its cpu_baseline)."""
     L, N = args.L, args.L * args.L
     return {"workload": f"SW sweep, 2D XY, L={L} periodic ({N} spins), beta={args.beta}, "
                         "FP32 angles, Philox random start",
             "L": L, "beta": args.beta, "tile": f"32x{args.tile_y or 'auto'}",
             "thresholds": "fp64-exact" if args.exact else "fp32",
             "parallelism": f"replicas x{ws}",
-            "l2": f"working set {N * 12.75 / 1e6:.0f} MB > 126 MB L2; no flush"}
+            "l2": (f"working set {N * 12.75 / 1e6:.0f} MB > 126 MB L2; no flush"
+                   if N * 12.75 > 126e6 else
+                   f"working set {N * 12.75 / 1e6:.1f} MB fits in L2; sweeps back to back")}
 
 
 def run_reference(args):
-    """The oracle timed as the reference arm (rank 0 only)."""
+    """The oracle timed as the reference arm (rank 0 only): its OpenMP build
+    on all host cores, one sweep of the benchmark lattice (L = --L) per
+    step -- the same workload and steps as the GPU arm."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import oracle
 
     oracle.build()
-    # bounded sample: one sweep of an L_s x L_s lattice per step, L_s the
-    # largest power of two with an estimated run under ~90 s (230 ns/site)
-    total = args.steps + args.warmup
-    L_s = 64
-    while L_s * 2 <= args.L and total * (2 * L_s) ** 2 * 230e-9 < 90.0:
-        L_s *= 2
-    th = oracle.init_angles(L_s, 1000, 0)
-    oracle.sw_run(th, L_s, L_s, args.beta, 1000, 0, args.warmup, record=False)
+    L = args.L
+    cores = os.cpu_count() or 1
+    threads = oracle.omp_threads(cores)
+    th = oracle.init_angles(L, 1000, 0)
+    oracle.sw_run(th, L, L, args.beta, 1000, 0, args.warmup, record=False, omp=True)
     t0 = time.perf_counter()
-    oracle.sw_run(th, L_s, L_s, args.beta, 1000, args.warmup, args.steps, record=False)
+    oracle.sw_run(th, L, L, args.beta, 1000, args.warmup, args.steps, record=False, omp=True)
     dt = time.perf_counter() - t0
-    v = args.steps * L_s * L_s / (dt * 1e9)
-    sample = f"{args.steps} sweeps of an L={L_s} lattice (beta={args.beta}) per run, one sweep per step"
+    v = args.steps * L * L / (dt * 1e9)
+    sample = (f"{args.steps} timed sweeps of the L={L} lattice (beta={args.beta}) after "
+              f"{args.warmup} warm-up sweeps, one sweep per step; OpenMP build on {threads} "
+              "threads (labeling sequential)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": bench_config(args, ws),
-        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -618,8 +741,13 @@ def main():
     ap.add_argument("--tile-y", dest="tile_y", type=int, default=64)
     ap.add_argument("--exact", type=int, default=0)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=50)
-    ap.add_argument("--cpu-sweeps", dest="cpu_sweeps", type=int, default=3)
-    ap.add_argument("--big-steps", dest="big_steps", type=int, default=10)
+    ap.add_argument("--cpu-sweeps", dest="cpu_sweeps", type=int, default=8)
+    ap.add_argument("--big-steps", dest="big_steps", type=int, default=100)
+    ap.add_argument("--big-therm", dest="big_therm", type=int, default=200)
+    ap.add_argument("--therm", type=int, default=1000)
+    ap.add_argument("--windows", type=int, default=5)
+    ap.add_argument("--window-sweeps", dest="window_sweeps", type=int, default=1000)
+    ap.add_argument("--no-protocol", dest="protocol", action="store_false")
     ap.add_argument("--no-big", dest="big", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-precision", dest="precision", action="store_false")

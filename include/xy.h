@@ -228,6 +228,18 @@ xy_status xy_get_sites(xy_lattice *h, const uint64_t *host_sites, uint32_t n,
  * angles, the sweep counter or the records. */
 xy_status xy_label_bonds(xy_lattice *h, const uint8_t *host_right,
                          const uint8_t *host_down, uint32_t *host_labels);
+/* Test and diagnostics: the iteration bound of every device-side global
+ * find, union and pointer-jumping loop of this lattice (cap = 0 restores the
+ * default, 2^22; a loop that reaches the bound stops, records the error and
+ * its launch completes, and the next synchronising call returns
+ * XY_ETIMEOUT).  No cluster of a valid lattice needs anywhere near the
+ * default; a test sets a tiny bound to make the bound run out on purpose.
+ * Synchronising. */
+xy_status xy_set_loop_bound(xy_lattice *h, uint32_t cap);
+/* The compute capability the library's device code was built for, as
+ * major * 10 + minor of the loaded kernel image (103 for sm_103a).  Needs a
+ * CUDA device. */
+xy_status xy_build_arch(int *binary_version);
 /* Diagnostics of exact mode since xy_init: bonds decided in FP64 (inside
  * the FP32 error band) and, among them, those where the FP32 decision would
  * have differed. */
@@ -257,7 +269,8 @@ xy_status xy_run_host_async(xy_lattice *h, const void *host_angles_in,
                             uint32_t n_sweeps, xy_obs *host_obs,
                             void *host_angles_out);
 /* Wait for everything enqueued on the lattice's stream; XY_ETIMEOUT if a
- * device loop hit its bound since the last check. */
+ * device loop hit its bound since the last check.  A device error is
+ * reported once: the call that reports it also clears it. */
 xy_status xy_sync(xy_lattice *h);
 
 /* ---- kernel timing ------------------------------------------------------- */
@@ -329,12 +342,16 @@ xy_status xy_engine_destroy(xy_engine *e);
  *   - L is limited to 2..XY_STATIC_MAX_L; larger L returns XY_EINVAL.
  *   - The first call on a device looks up the scratch's device address
  *     (cudaGetSymbolAddress) for that device; make that first call before
- *     any stream capture.
+ *     any stream capture (during capture a first call returns XY_EINVAL).
+ *     Every later call outside stream capture looks it up again, so a
+ *     cudaDeviceReset between calls is followed correctly.  Bond bytes are
+ *     active when nonzero (xy_label_bonds, by contrast, takes only 0 / 1).
  *   - All calls share the scratch: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and give wrong labels.
  *   - Work is enqueued on cuda_stream; sync = 1 waits for it and reports a
- *     device-side loop bound as XY_ETIMEOUT, sync = 0 returns after
- *     enqueueing (errors then go unreported). */
+ *     device-side loop bound as XY_ETIMEOUT (any other device error as
+ *     XY_EINTERNAL), sync = 0 returns after enqueueing (errors then go
+ *     unreported). */
 #define XY_STATIC_MAX_L 1024u
 xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right,
                                 const uint8_t *d_down, uint32_t *d_labels,

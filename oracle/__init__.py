@@ -21,23 +21,33 @@ import numpy as np
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "oracle.c"
 _LIB = _HERE / "liboracle.so"
+# the same source built with -fopenmp: bonds, flip and observables on all
+# host cores (labeling sequential); used only to time the CPU baseline
+_LIB_OMP = _HERE / "liboracle_omp.so"
 
 _lib = None
+_lib_omp = None
 
 
-def build(force: bool = False) -> Path:
-    """Compile oracle.c into liboracle.so with plain IEEE FP64 semantics."""
-    if force or not _LIB.exists() or _LIB.stat().st_mtime < max(
+def _compile(out: Path, extra: list, force: bool):
+    if force or not out.exists() or out.stat().st_mtime < max(
         _SRC.stat().st_mtime, (_HERE / "oracle.h").stat().st_mtime
     ):
-        tmp = _LIB.with_suffix(f".so.tmp{os.getpid()}")
+        tmp = out.with_suffix(f".so.tmp{os.getpid()}")
         cmd = [
             "gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-            "-ffp-contract=off", "-fno-fast-math",
+            "-ffp-contract=off", "-fno-fast-math", *extra,
             str(_SRC), "-o", str(tmp), "-lm",
         ]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+        os.replace(tmp, out)
+
+
+def build(force: bool = False) -> Path:
+    """Compile oracle.c into liboracle.so with plain IEEE FP64 semantics, and
+    the OpenMP timing build liboracle_omp.so."""
+    _compile(_LIB, [], force)
+    _compile(_LIB_OMP, ["-fopenmp"], force)
     return _LIB
 
 
@@ -45,19 +55,27 @@ class Sums(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "sum_cos", "sum_sin", "sum_cos_r", "sum_sin_r", "sum_cos_d",
         "sum_sin_d", "n_sites", "n_links_r", "n_links_d")] + [
-        ("fx", ctypes.c_double * 4), ("fy", ctypes.c_double * 4)]
+        ("fx", ctypes.c_double * 4), ("fy", ctypes.c_double * 4)] + [
+        (n, ctypes.c_double) for n in ("abs_cos", "abs_sin", "abs_cos_r", "abs_sin_r",
+                                       "abs_cos_d", "abs_sin_d")]
 
 
 OBS_FIELDS = ("energy_per_site", "m2", "mx", "my", "ex", "sx", "ey", "sy",
               "upsilon", "beta", "chik")
 
 
+# L1 norms per site of the sums behind mx, my, ex, sx, ey, sy (sum |term| / N):
+# the scale a cancelling sum is compared against (tolerance reading A19)
+L1_FIELDS = ("l1_mx", "l1_my", "l1_ex", "l1_sx", "l1_ey", "l1_sy")
+
+
 class Obs(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in OBS_FIELDS + ("flipped",)]
+    _fields_ = [(n, ctypes.c_double) for n in OBS_FIELDS + ("flipped",) + L1_FIELDS]
 
 
-# per-update records: the observables and the number of reflected sites
-OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS + ("flipped",)])
+# per-update records: the observables, the number of reflected sites and the
+# L1 norms
+OBS_DTYPE = np.dtype([(n, np.float64) for n in OBS_FIELDS + ("flipped",) + L1_FIELDS])
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -66,12 +84,14 @@ _U64 = ctypes.c_uint64
 _D = ctypes.c_double
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The plain oracle library, or (omp=True) its OpenMP timing build."""
+    global _lib, _lib_omp
+    if (_lib_omp if omp else _lib) is None:
         build()
-        L = ctypes.CDLL(str(_LIB))
+        L = ctypes.CDLL(str(_LIB_OMP if omp else _LIB))
         sig = {
+            "orc_threads": (_I, [_I]),
             "orc_philox4x32_10": (None, [_P, _P, _P]),
             "orc_philox_stream": (None, [_U64, _P, _I, _U64, _P]),
             "orc_axis": (None, [_U64, _U32, _P, _P]),
@@ -113,8 +133,16 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
-        _lib = L
-    return _lib
+        if omp:
+            _lib_omp = L
+        else:
+            _lib = L
+    return _lib_omp if omp else _lib
+
+
+def omp_threads(n: int = 0) -> int:
+    """Threads of the OpenMP timing build (n > 0 sets them); returns the count."""
+    return int(lib(omp=True).orc_threads(n))
 
 
 def _ptr(a: np.ndarray):
@@ -252,7 +280,7 @@ def sums(theta: np.ndarray, Lx: int, Ly: int, per_x: int = 1, per_y: int = 1) ->
 def derive(s: Sums, beta: float) -> dict:
     o = Obs()
     lib().orc_derive(ctypes.byref(s), beta, ctypes.byref(o))
-    return {n: getattr(o, n) for n in OBS_FIELDS}
+    return {n: getattr(o, n) for n in OBS_FIELDS + L1_FIELDS}
 
 
 def measure(theta: np.ndarray, Lx: int, Ly: int, beta: float, per_x: int = 1, per_y: int = 1) -> dict:
@@ -277,12 +305,18 @@ class _Scratch:
 
 
 def sw_run(theta: np.ndarray, Lx: int, Ly: int, beta: float, seed: int, t0: int, n: int,
-           per_x: int = 1, per_y: int = 1, record: bool = True) -> np.ndarray:
-    """n fixed-beta sweeps t0..t0+n-1 in place; returns the per-sweep records."""
+           per_x: int = 1, per_y: int = 1, record: bool = True, omp: bool = False) -> np.ndarray:
+    """n fixed-beta sweeps t0..t0+n-1 in place; returns the per-sweep records.
+    omp=True runs the OpenMP timing build (FP32 angles only)."""
     sc = _Scratch(Lx * Ly)
     obs = np.zeros(n, OBS_DTYPE) if record else None
     optr = _ptr(obs) if record else None
-    if theta.dtype == np.float32:
+    if omp:
+        assert theta.dtype == np.float32
+        lib(omp=True).orc_sw_run_f32(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t0, n,
+                                     _ptr(sc.right), _ptr(sc.down), _ptr(sc.label),
+                                     _ptr(sc.queue), optr)
+    elif theta.dtype == np.float32:
         lib().orc_sw_run_f32(Lx, Ly, per_x, per_y, _ptr(theta), beta, seed, t0, n,
                              _ptr(sc.right), _ptr(sc.down), _ptr(sc.label), _ptr(sc.queue), optr)
     elif theta.dtype == np.uint16:

@@ -247,6 +247,7 @@ static long bonds_generic(int Lx, int Ly, int per_x, int per_y,
                           uint8_t *right, uint8_t *down) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long band = 0;
+#pragma omp parallel for schedule(static) reduction(+ : band)
   for (uint64_t i = 0; i < n; ++i) {
     uint32_t w_right, w_down;
     bond_words(seed, t, Lx, i, &w_right, &w_down);
@@ -274,18 +275,21 @@ static long bonds_generic(int Lx, int Ly, int per_x, int per_y,
 
 static double *widen_f32(const float *theta, uint64_t n) {
   double *ang = (double *)malloc(n * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < n; ++i) ang[i] = (double)theta[i];
   return ang;
 }
 
 static double *widen_f16(const uint16_t *bits, uint64_t n) {
   double *ang = (double *)malloc(n * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < n; ++i) ang[i] = (double)half_bits_to_float(bits[i]);
   return ang;
 }
 
 static double *widen_u16(const uint16_t *q, uint64_t n) {
   double *ang = (double *)malloc(n * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < n; ++i) ang[i] = (double)q[i] * ORC_U16_STEP;
   return ang;
 }
@@ -482,6 +486,7 @@ long orc_flip_f32(int Lx, int Ly, float *theta, const uint32_t *label,
                   uint64_t seed, uint32_t t, float c32, uint8_t *flipped) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long count = 0;
+#pragma omp parallel for schedule(static) reduction(+ : count)
   for (uint64_t i = 0; i < n; ++i) {
     int f = orc_coin(seed, t, Lx, label[i]);
     if (flipped) flipped[i] = (uint8_t)f;
@@ -497,6 +502,7 @@ long orc_flip_f16(int Lx, int Ly, uint16_t *theta_bits, const uint32_t *label,
                   uint64_t seed, uint32_t t, float c32, uint8_t *flipped) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long count = 0;
+#pragma omp parallel for schedule(static) reduction(+ : count)
   for (uint64_t i = 0; i < n; ++i) {
     int f = orc_coin(seed, t, Lx, label[i]);
     if (flipped) flipped[i] = (uint8_t)f;
@@ -514,6 +520,7 @@ long orc_flip_u16(int Lx, int Ly, uint16_t *q, const uint32_t *label,
                   uint64_t seed, uint32_t t, uint16_t cq, uint8_t *flipped) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long count = 0;
+#pragma omp parallel for schedule(static) reduction(+ : count)
   for (uint64_t i = 0; i < n; ++i) {
     int f = orc_coin(seed, t, Lx, label[i]);
     if (flipped) flipped[i] = (uint8_t)f;
@@ -532,12 +539,17 @@ static void sums_generic(int Lx, int Ly, int per_x, int per_y,
                          const double *ang, orc_sums *s) {
   uint64_t n = (uint64_t)Lx * (uint64_t)Ly;
   long double c = 0, sn = 0, cr = 0, sr = 0, cd = 0, sd = 0;
+  long double ac = 0, asn = 0, acr = 0, asr = 0, acd = 0, asd = 0;
   long double fx[4] = {0, 0, 0, 0}, fy[4] = {0, 0, 0, 0};
   uint64_t nr = 0, nd = 0;
+#pragma omp parallel for schedule(static) \
+    reduction(+ : c, sn, cr, sr, cd, sd, ac, asn, acr, asr, acd, asd, nr, nd, fx[:4], fy[:4])
   for (uint64_t i = 0; i < n; ++i) {
     double ci = cos(ang[i]), si = sin(ang[i]);
     c += ci;
     sn += si;
+    ac += fabs(ci);
+    asn += fabs(si);
     uint64_t x = i % (uint64_t)Lx, y = i / (uint64_t)Lx;
     double kx = ORC_TWO_PI * (double)x / (double)Lx;
     double ky = ORC_TWO_PI * (double)y / (double)Ly;
@@ -554,12 +566,16 @@ static void sums_generic(int Lx, int Ly, int per_x, int per_y,
       double d = ang[i] - ang[j];
       cr += cos(d);
       sr += sin(d);
+      acr += fabs(cos(d));
+      asr += fabs(sin(d));
       ++nr;
     }
     if (down_of(Lx, Ly, per_y, i, &j)) {
       double d = ang[i] - ang[j];
       cd += cos(d);
       sd += sin(d);
+      acd += fabs(cos(d));
+      asd += fabs(sin(d));
       ++nd;
     }
   }
@@ -572,6 +588,12 @@ static void sums_generic(int Lx, int Ly, int per_x, int per_y,
   s->n_sites = (double)n;
   s->n_links_r = (double)nr;
   s->n_links_d = (double)nd;
+  s->abs_cos = (double)ac;
+  s->abs_sin = (double)asn;
+  s->abs_cos_r = (double)acr;
+  s->abs_sin_r = (double)asr;
+  s->abs_cos_d = (double)acd;
+  s->abs_sin_d = (double)asd;
   for (int k = 0; k < 4; ++k) {
     s->fx[k] = (double)fx[k];
     s->fy[k] = (double)fy[k];
@@ -622,6 +644,12 @@ void orc_derive(const orc_sums *s, double beta, orc_obs *o) {
   }
   o->chik = (ax + ay) / (2.0 * n);
   o->flipped = 0.0; /* set by the update that produced the configuration */
+  o->l1_mx = s->abs_cos / n;
+  o->l1_my = s->abs_sin / n;
+  o->l1_ex = s->abs_cos_r / n;
+  o->l1_sx = s->abs_sin_r / n;
+  o->l1_ey = s->abs_cos_d / n;
+  o->l1_sy = s->abs_sin_d / n;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -637,6 +665,27 @@ double orc_pcc_next_beta(double beta, double beta_upsilon, double target,
 double orc_pcc_dbeta(double dbeta0, uint32_t halve_every, uint32_t k) {
   if (halve_every == 0) return dbeta0;
   return ldexp(dbeta0, -(int)(k / halve_every));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Threads.  The same source is built twice: plainly (the oracle the tests   */
+/* use; the OpenMP pragmas above are ignored) and with -fopenmp, where the   */
+/* bond, flip and observable loops run on all host cores and the labeling    */
+/* stays sequential.  The OpenMP build only times the CPU baseline; its      */
+/* parallel sums add the same terms in another order.                        */
+/* ------------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */

@@ -69,6 +69,10 @@ typedef struct {
    * sin th sin kx) with kx = 2 pi x / Lx; fy[] the same with y. */
   double fx[4];
   double fy[4];
+  /* L1 norms of the six sums above (sum of |term|): the scale against which
+   * a sum that cancels (m, s_x, s_y, or e near infinite temperature) is
+   * compared (tolerance reading A19) */
+  double abs_cos, abs_sin, abs_cos_r, abs_sin_r, abs_cos_d, abs_sin_d;
 } orc_sums;
 
 /* Derived per-configuration observables. */
@@ -84,7 +88,14 @@ typedef struct {
                               configuration's chi at the smallest nonzero
                               wave vector, averaged over x and y (Eq. (9)) */
   double flipped;          /* sites the update reflected (0 from derive)   */
+  /* the L1 norms per site of the sums behind mx, my, ex, sx, ey, sy */
+  double l1_mx, l1_my, l1_ex, l1_sx, l1_ey, l1_sy;
 } orc_obs;
+
+/* Threads of the loops that run in parallel in the OpenMP build (bonds,
+ * flip, observables; the labeling is sequential): n > 0 sets the count;
+ * returns the count in use (always 1 in the plain build). */
+int orc_threads(int n);
 
 /* ---- Philox4x32-10 ------------------------------------------------------ */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],

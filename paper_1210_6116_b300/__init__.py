@@ -53,12 +53,14 @@ EXPORTS = (
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
     "xy_get_bonds", "xy_get_labels", "xy_get_sites", "xy_get_spins", "xy_label_bonds", "xy_get_band_stats",
     "xy_save", "xy_load", "xy_run_host", "xy_run_host_async", "xy_sync", "xy_profile",
-    "xy_profile_read", "xy_label_bonds_static",
+    "xy_profile_read", "xy_label_bonds_static", "xy_set_loop_bound", "xy_build_arch",
     "xy_engine_workspace_size", "xy_engine_create", "xy_engine_admit", "xy_engine_retire",
     "xy_engine_step", "xy_engine_measure", "xy_engine_get_angles", "xy_engine_get_state",
     "xy_engine_destroy",
 )
 KERNEL_NAMES = ("bond_label", "merge", "compress", "flip_measure", "finalize")
+# kernel launches of one single-lattice sweep (xy_sweep adds one per call)
+LAUNCHES_PER_SWEEP = 5
 
 
 class XyError(RuntimeError):
@@ -136,6 +138,8 @@ def load_library() -> ctypes.CDLL:
         "xy_profile": (I, [P, I]),
         "xy_profile_read": (I, [P, P]),
         "xy_label_bonds_static": (I, [U32, P, P, P, P, I]),
+        "xy_set_loop_bound": (I, [P, U32]),
+        "xy_build_arch": (I, [P]),
         "xy_engine_workspace_size": (I, [U32, P]),
         "xy_engine_create": (I, [U32, I, I, U32, P, ctypes.c_size_t, P, P]),
         "xy_engine_admit": (I, [P, P, P, P, ctypes.c_size_t, P]),
@@ -209,6 +213,13 @@ def xy_destroy(h):
 
 def xy_last_error() -> str:
     return load_library().xy_last_error().decode()
+
+
+def xy_build_arch() -> int:
+    """Compute capability of the loaded device code (103 for sm_103a)."""
+    v = ctypes.c_int(0)
+    _check(load_library().xy_build_arch(ctypes.byref(v)))
+    return v.value
 
 
 XY_STATIC_MAX_L = 1024
@@ -319,6 +330,10 @@ class Lattice:
         out = np.zeros(self.n, np.uint32)
         _check(load_library().xy_label_bonds(self.handle, _ptr(r), _ptr(d), _ptr(out)))
         return out
+
+    def set_loop_bound(self, cap: int):
+        """Bound on the device-side find/union loops (0: the default)."""
+        _check(load_library().xy_set_loop_bound(self.handle, int(cap)))
 
     def band_stats(self):
         a = ctypes.c_uint64(0)

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 
 #include "../../include/xy.h"
 #include "sweep_kernels.cuh"
@@ -19,6 +20,23 @@ inline xy_status layout_fail(xy_status s, const char *msg) {
 }
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Status for a lattice's device error word (DevState::err): a bounded
+// find / union / jump loop that ran out is XY_ETIMEOUT, any other recorded
+// error XY_EINTERNAL.  Every entry point that reports device errors maps the
+// word through here, so they agree.
+inline xy_status device_error_status(uint32_t err) {
+  char msg[128];
+  if (err & (kErrFindCap | kErrUnionCap)) {
+    snprintf(msg, sizeof(msg), "device-side find/union loop hit its bound (err=%#x)", err);
+    return layout_fail(XY_ETIMEOUT, msg);
+  }
+  if (err) {
+    snprintf(msg, sizeof(msg), "device error word %#x", err);
+    return layout_fail(XY_EINTERNAL, msg);
+  }
+  return XY_OK;
+}
 
 inline uint32_t default_tile_y(uint32_t L) {
   if (L <= 32) return 16;
@@ -112,6 +130,7 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.xi = cfg->measure_xi ? 1u : 0u;
   d.wolff = cfg->update == XY_UPDATE_WOLFF ? 1u : 0u;
   d.wave = reinterpret_cast<const float2 *>(ws + lo.off_wave);
+  d.find_cap = kFindCap;
   d.acc = reinterpret_cast<long long *>(ws + lo.off_acc);
   d.st = reinterpret_cast<DevState *>(ws + lo.off_state);
   d.rec = reinterpret_cast<ObsRecord *>(ws + lo.off_rec);

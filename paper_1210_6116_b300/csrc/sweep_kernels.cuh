@@ -43,7 +43,9 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kSlots = 64;             // accumulator slots per lattice
 constexpr int kAccStride = 16;         // int64 per slot (6, or 14 with xi; [15] flips)
 constexpr int kFlipSlot = 15;          // slot entry counting the reflected sites
-constexpr uint32_t kFindCap = 1u << 22;  // bound on any global find / union loop
+// default bound on the iterations of any global find / union / jump loop
+// (LatDesc::find_cap; a test may lower it to make the bound run out)
+constexpr uint32_t kFindCap = 1u << 22;
 
 // error bits recorded in DevState::err
 constexpr uint32_t kErrFindCap = 1u;
@@ -93,6 +95,7 @@ struct LatDesc {
   double inv_n;     // 1 / L^2
   uint32_t xi;     // 1: accumulate the Fourier sums of chik
   uint32_t wolff;  // 1: Wolff single-cluster update (reflect the seed's cluster)
+  uint32_t find_cap;  // iteration bound of the global find / union / jump loops
   const float2 *wave;  // [L]: (cos, sin)(2 pi x / L), used when xi
   void *theta[2];
   uint32_t *label;
@@ -359,8 +362,8 @@ __device__ __forceinline__ void sunion(uint32_t *par, uint32_t a, uint32_t b) {
 // ---------------------------------------------------------------------------
 // find with path halving; only used while no other kernel reads labels
 __device__ __forceinline__ uint32_t gfind_halve(uint32_t *lab, uint32_t a,
-                                                DevState *st) {
-  for (uint32_t it = 0; it < kFindCap; ++it) {
+                                                DevState *st, uint32_t cap) {
+  for (uint32_t it = 0; it < cap; ++it) {
     const uint32_t p = __ldcg(lab + a);
     if (p == a) return a;
     const uint32_t gp = __ldcg(lab + p);
@@ -371,29 +374,17 @@ __device__ __forceinline__ uint32_t gfind_halve(uint32_t *lab, uint32_t a,
   return a;
 }
 
-// read-only find
-__device__ __forceinline__ uint32_t gfind_ro(const uint32_t *lab, uint32_t a,
-                                             DevState *st) {
-  for (uint32_t it = 0; it < kFindCap; ++it) {
-    const uint32_t p = __ldcg(lab + a);
-    if (p == a) return a;
-    a = p;
-  }
-  atomicOr(&st->err, kErrFindCap);
-  return a;
-}
-
 // A successful link of root a is appended to the calling tile's link slots
 // (at most one per call, so the tile's edge-item count bounds them; one
 // counter per tile keeps the appends from piling onto one address):
 // k_compress jumps exactly those roots.
 __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
-                                       DevState *st, uint32_t *links, uint32_t *count,
-                                       uint32_t cap) {
-  a = gfind_halve(lab, a, st);
-  b = gfind_halve(lab, b, st);
+                                       DevState *st, uint32_t fcap, uint32_t *links,
+                                       uint32_t *count, uint32_t cap) {
+  a = gfind_halve(lab, a, st, fcap);
+  b = gfind_halve(lab, b, st, fcap);
   for (uint32_t it = 0; a != b; ++it) {
-    if (it >= kFindCap) {
+    if (it >= fcap) {
       atomicOr(&st->err, kErrUnionCap);
       return;
     }
@@ -409,8 +400,8 @@ __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
       else atomicOr(&st->err, kErrLinkCap);
       return;
     }
-    a = gfind_halve(lab, old, st);
-    b = gfind_halve(lab, b, st);
+    a = gfind_halve(lab, old, st, fcap);
+    b = gfind_halve(lab, b, st, fcap);
   }
 }
 
@@ -825,7 +816,7 @@ __global__ void __launch_bounds__(kThreads)
   const unsigned long long key =
       e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
   if (group_leader(key, e.rep) && e.act)
-    gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u),
+    gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->find_cap, e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u),
            e.d->link_count + e.tile, TY + 32u);
 }
 
@@ -833,8 +824,8 @@ __global__ void __launch_bounds__(kThreads)
 // root.  When all linked roots jump concurrently, a chain of length d
 // collapses in O(log d) steps per node instead of a walk of length d.  Only
 // ancestors are ever written and roots no longer change.
-__device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st) {
-  for (uint32_t it = 0; it < kFindCap; ++it) {
+__device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st, uint32_t cap) {
+  for (uint32_t it = 0; it < cap; ++it) {
     const uint32_t p = __ldcg(lab + x);
     if (p == x) return;
     const uint32_t gp = __ldcg(lab + p);
@@ -866,7 +857,7 @@ __global__ void __launch_bounds__(kThreads)
   // slots; past the count it holds an older sweep's entry and is not used)
   const uint32_t count = __ldcg(d.link_count + tile);
   const uint32_t x = __ldcg(d.links + static_cast<uint64_t>(tile) * per + j);
-  if (j < count) jump(d.label, x, d.st);
+  if (j < count) jump(d.label, x, d.st, d.find_cap);
 }
 
 // ---------------------------------------------------------------------------

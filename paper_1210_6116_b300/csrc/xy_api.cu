@@ -225,13 +225,14 @@ cudaError_t launch_label_only(xy_lattice *h) {
   }
 }
 
+// Report the lattice's device error word and clear it: an error is reported
+// once, and the handle stays usable (the kernels that set the word finished
+// their launches; the labels of the affected sweep are not meaningful).
 xy_status check_device_error(xy_lattice *h) {
   uint32_t err = 0;
   XY_CUDA(cudaMemcpy(&err, &h->d_state->err, sizeof(err), cudaMemcpyDeviceToHost));
-  if (err & (kErrFindCap | kErrUnionCap))
-    return fail(XY_ETIMEOUT, "device-side find/union loop hit its bound (err=%#x)", err);
-  if (err) return fail(XY_EINTERNAL, "device error word %#x", err);
-  return XY_OK;
+  if (err) XY_CUDA(cudaMemset(&h->d_state->err, 0, sizeof(err)));
+  return device_error_status(err);
 }
 
 }  // namespace
@@ -660,6 +661,22 @@ xy_status xy_label_bonds(xy_lattice *h, const uint8_t *host_right, const uint8_t
   if (s != XY_OK) return s;
   XY_CUDA(cudaMemcpy(host_labels, h->desc.label, static_cast<size_t>(L) * L * 4,
                      cudaMemcpyDeviceToHost));
+  return XY_OK;
+}
+
+xy_status xy_build_arch(int *binary_version) {
+  if (!binary_version) return fail(XY_EINVAL, "binary_version is NULL");
+  cudaFuncAttributes a{};
+  XY_CUDA(cudaFuncGetAttributes(&a, k_finalize));
+  *binary_version = a.binaryVersion;
+  return XY_OK;
+}
+
+xy_status xy_set_loop_bound(xy_lattice *h, uint32_t cap) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  h->desc.find_cap = cap ? cap : kFindCap;
+  XY_CUDA(cudaMemcpy(h->d_desc, &h->desc, sizeof(LatDesc), cudaMemcpyHostToDevice));
   return XY_OK;
 }
 

@@ -299,7 +299,10 @@ xy_status xy_engine_measure(xy_engine *e, uint32_t slot, xy_obs *out, uint32_t m
   XY_CUDA(cudaStreamSynchronize(e->stream));
   uint32_t err = 0;
   XY_CUDA(cudaMemcpy(&err, &s.desc.st->err, sizeof(err), cudaMemcpyDeviceToHost));
-  if (err) return fail(XY_ETIMEOUT, "device-side loop bound hit in slot %u (err=%#x)", slot, err);
+  if (err) {
+    XY_CUDA(cudaMemset(&s.desc.st->err, 0, sizeof(err)));  // reported once
+    return device_error_status(err);
+  }
   const uint64_t pending = s.enqueued - s.reported;
   const uint64_t take = std::min<uint64_t>(std::min<uint64_t>(pending, s.lo.rec_cap), max_records);
   const uint64_t first = s.enqueued - take;

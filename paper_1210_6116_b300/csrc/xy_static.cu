@@ -21,12 +21,10 @@
 #include <mutex>
 
 #include "../../include/xy.h"
+#include "layout.cuh"
 #include "sweep_kernels.cuh"
 
 using namespace xyk;
-
-// defined in xy_api.cu: the thread's xy_last_error() message
-void xy_set_last_error_message(const char *msg);
 
 namespace {
 
@@ -63,18 +61,28 @@ xy_status fail(xy_status s, const char *fmt, ...) {
   return s;
 }
 
-// device address of the scratch, looked up once per device
+// Device address of the scratch on each device.  It is looked up (with that
+// device current) by the first call on the device, and looked up again by
+// every call made outside stream capture: a cudaDeviceReset ends the context
+// the address belonged to, and the next call outside capture then picks up
+// the address in the new context.  A call made while its stream is being
+// captured uses the address of the last call outside capture.
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_setup_mutex;
 
-xy_status scratch_for_current_device(unsigned char **out) {
+xy_status scratch_for_current_device(cudaStream_t stream, unsigned char **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(XY_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(XY_EUNSUPPORTED, "device %d out of range", dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return fail(XY_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(XY_EINVAL, "the first call on a device must come before any stream capture");
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_label_scratch);
     if (e != cudaSuccess)
@@ -129,10 +137,10 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
     return fail(XY_EINVAL, "L = %u outside 2..%u (the size of the built-in scratch)", L,
                 XY_STATIC_MAX_L);
   if (!d_right || !d_down || !d_labels) return fail(XY_EINVAL, "NULL device pointer");
-  unsigned char *scratch = nullptr;
-  xy_status s = scratch_for_current_device(&scratch);
-  if (s != XY_OK) return s;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  unsigned char *scratch = nullptr;
+  xy_status s = scratch_for_current_device(stream, &scratch);
+  if (s != XY_OK) return s;
 
   LatDesc d{};
   d.L = L;
@@ -149,6 +157,7 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   d.links = reinterpret_cast<uint32_t *>(scratch + kOffLinks);
   d.link_count = reinterpret_cast<uint32_t *>(scratch + kOffLinkCount);
   d.st = reinterpret_cast<DevState *>(scratch + kOffState);
+  d.find_cap = kFindCap;
   LatDesc *d_desc = reinterpret_cast<LatDesc *>(scratch + kOffDesc);
   uint32_t *d_prefix = reinterpret_cast<uint32_t *>(scratch + kOffPrefix);
   const uint32_t nw = d.ntiles;
@@ -173,8 +182,7 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   uint32_t err = 0;
   e = cudaMemcpy(&err, &d.st->err, sizeof(err), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(XY_ECUDA, "error word: %s", cudaGetErrorString(e));
-  if (err) return fail(XY_ETIMEOUT, "device-side find/union loop hit its bound (err=%#x)", err);
-  return XY_OK;
+  return device_error_status(err);  // the setup kernel clears the word on every call
 }
 
 }  // extern "C"

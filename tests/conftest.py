@@ -19,3 +19,20 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With XY_OBS_ERRLOG set, write the largest observable errors the GPU
+    parity tests measured (gpu_helpers.measured_errors) to that file."""
+    path = os.environ.get("XY_OBS_ERRLOG")
+    if not path:
+        return
+    try:
+        import gpu_helpers
+    except ImportError:
+        return
+    errs = gpu_helpers.measured_errors()
+    if errs:
+        import json
+        Path(path).parent.mkdir(parents=True, exist_ok=True)
+        Path(path).write_text(json.dumps(errs, indent=1, sort_keys=True))

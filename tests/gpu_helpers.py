@@ -1,35 +1,62 @@
 """Shared helpers of the GPU parity tests: tolerances and record comparison.
 
-Tolerances, derived from the arithmetic of the observable kernel.  Each site
-term is evaluated in FP32 from the stored angles: cos/sin of an angle with
-the kernel's own routine (Cody-Waite reduction and Taylor polynomials,
-<= 1e-7 absolute, measured in test_gpu_spins; the bounds below allow
-1.2e-7), and a link
-term cos(ti - tj) = ci cj + si sj (or si cj - ci sj) with error
-<= 1.2e-7 * (|ci| + |cj| + |si| + |sj|) + 1.2e-7 <= 4.6e-7.  Every term is then
-rounded to a 2^-22 grid (<= 2^-23 = 1.2e-7) and summed exactly in integers.
-Per site, a link sum (e_x, s_x, e_y, s_y) is therefore within
-EPS_LINK = 6e-7 of the oracle's FP64 sum / N, a site sum (m_x, m_y) within
-EPS_SITE = 2.4e-7, and E/site (two links per site) within 2 EPS_LINK.
-The 1e-6 relative target for the observables holds on top of these wherever the value is
-O(1) (E/site ~ -1.4, e_x ~ 0.7): the test takes max(1e-6 |value|, bound).
-M^2 = mx^2 + my^2 and Upsilon = e_x - beta N s_x^2 inherit the bounds by
-error propagation.
+Observable tolerance (reading A19 of the hot-path scope: 1e-6 relative, with
+sums that cancel compared against their L1 norm).  With REL = 1e-6 and, from
+the oracle's record, l1_q = N^-1 sum |term| of the sum behind q:
+
+    E/site, e_x, e_y, m_x, m_y, s_x, s_y   REL * l1_q
+    Upsilon = e_x - beta N s_x^2           REL * (l1_ex + beta N s_x^2)
+    M^2 = m_x^2 + m_y^2                    REL * max(M^2, |m_x| l1_mx + |m_y| l1_my)
+
+For a sum that does not cancel (the ordered and critical configurations the
+method runs at: E/site ~ -1.4, e_x ~ 0.7, M^2 = O(0.1 .. 1)) l1_q = |q| and
+these are exactly 1e-6 relative; l1_q only matters where the terms cancel
+(m, s, and e near infinite temperature).  Upsilon is compared against the
+magnitudes of its two terms, and no term of any tolerance grows with N.
+
+The kernel's error is far below these: every term is an FP32 product of the
+kernel's own cos/sin (absolute error <= 1e-7, test_gpu_spins), rounded to a
+2^-22 grid and summed exactly in integers, so the error of a per-site mean is
+a sum of N independent roundings divided by N.  measured_errors() keeps the
+largest error / tolerance seen per field; conftest writes it out when
+XY_OBS_ERRLOG names a file.
 
 chik (Eq. (9) at the smallest wave vector) is built from eight Fourier sums
-F_c = sum_r {cos, sin}(theta_r) {cos, sin}(2 pi x / L).  Each term is the
-product of an FP32 cos/sin (<= 1.2e-7), a wave factor rounded from FP64 to
-FP32 (<= 6e-8), the product's rounding (<= 6e-8) and the 2^-22 grid
-(<= 1.2e-7): EPS_WAVE = 3.6e-7 per term, so |dF_c| <= dF = EPS_WAVE N.  With
-sum_c |F_c| <= sqrt(8 sum_c F_c^2) = 4 sqrt(N chik), the error of
-chik = sum_c F_c^2 / (2N) is at most (4 dF sqrt(N chik) + 4 dF^2) / N.
+F_c = sum_r {cos, sin}(theta_r) {cos, sin}(2 pi x / L) of terms within
+EPS_WAVE = 3.6e-7 (FP32 cos/sin 1.2e-7, wave factor rounded from FP64 6e-8,
+product rounding 6e-8, 2^-22 grid 1.2e-7), so |dF_c| <= dF = EPS_WAVE N; with
+sum_c |F_c| <= 4 sqrt(N chik) the error of chik = sum_c F_c^2 / (2N) is at
+most (4 dF sqrt(N chik) + 4 dF^2) / N (reading A20).
 """
 import numpy as np
 
 REL = 1e-6
-EPS_LINK = 6e-7
-EPS_SITE = 2.4e-7
 EPS_WAVE = 3.6e-7
+
+_worst: dict = {}
+
+
+def measured_errors() -> dict:
+    """Largest |gpu - oracle| / tolerance (and the error itself) per field."""
+    return dict(_worst)
+
+
+def _note(k, err, tol, val):
+    w = _worst.get(k)
+    r = err / tol if tol > 0 else (0.0 if err == 0 else float("inf"))
+    if w is None or r > w["err_over_tol"]:
+        _worst[k] = {"err_over_tol": r, "abs_err": err,
+                     "rel_err": err / abs(val) if val else None}
+
+
+def obs_tolerances(o: dict, N: int, beta: float) -> dict:
+    """Tolerance of each compared observable, from the oracle record o."""
+    tol = {"energy_per_site": REL * (o["l1_ex"] + o["l1_ey"])}
+    for k in ("ex", "sx", "ey", "sy", "mx", "my"):
+        tol[k] = REL * o["l1_" + k]
+    tol["upsilon"] = REL * (o["l1_ex"] + beta * N * o["sx"] ** 2)
+    tol["m2"] = REL * max(o["m2"], abs(o["mx"]) * o["l1_mx"] + abs(o["my"]) * o["l1_my"])
+    return tol
 
 
 def obs_close(g: dict, o: dict, N: int, beta: float, xi: bool = False, flips: bool = False):
@@ -40,20 +67,13 @@ def obs_close(g: dict, o: dict, N: int, beta: float, xi: bool = False, flips: bo
     bad = []
 
     def chk(k, tol):
-        if abs(g[k] - o[k]) > tol:
+        err = abs(g[k] - o[k])
+        _note(k, err, tol, o[k])
+        if err > tol:
             bad.append((k, g[k], o[k], tol))
 
-    chk("energy_per_site", max(REL * abs(o["energy_per_site"]), 2 * EPS_LINK))
-    for k in ("ex", "ey"):
-        chk(k, max(REL * abs(o[k]), EPS_LINK))
-    for k in ("sx", "sy"):
-        chk(k, EPS_LINK)
-    for k in ("mx", "my"):
-        chk(k, EPS_SITE)
-    chk("m2", max(REL * o["m2"],
-                  2 * (abs(o["mx"]) + abs(o["my"]) + EPS_SITE) * EPS_SITE))
-    chk("upsilon", max(REL * abs(o["upsilon"]),
-                       EPS_LINK + beta * N * (2 * abs(o["sx"]) + EPS_LINK) * EPS_LINK))
+    for k, tol in obs_tolerances(o, N, beta).items():
+        chk(k, tol)
     if xi:
         dF = EPS_WAVE * N
         chk("chik", max(REL * o["chik"], (4 * dF * np.sqrt(N * o["chik"]) + 4 * dF * dF) / N))

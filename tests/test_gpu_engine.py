@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import synth
+from gpu_helpers import obs_close, rec_dict
 
 pytestmark = pytest.mark.gpu
 
@@ -98,8 +99,12 @@ def test_engine_lattice_matches_oracle(orc):
     eng.admit(eng.config(64, 1.3, 78))
     eng.step(20)
     th = orc.init_angles(96, 77, 0)
-    orc.sw_run(th, 96, 96, 1.12, 77, 0, 20, record=False)
+    orecs = orc.sw_run(th, 96, 96, 1.12, 77, 0, 20)
     np.testing.assert_array_equal(eng.get_angles(s0), th)
+    recs = eng.measure(s0)
+    assert len(recs) == 20
+    for k in range(20):  # observables of every sweep (Eqs. (3)-(6))
+        assert not obs_close(rec_dict(recs[k]), rec_dict(orecs[k]), 96 * 96, 1.12), k
 
 
 def test_engine_rejects_bad_lattices():

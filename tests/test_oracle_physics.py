@@ -55,6 +55,27 @@ def test_observables_twisted_y(orc, L, k):
     assert o["upsilon"] == pytest.approx(1.0, abs=1e-12)
 
 
+@pytest.mark.parametrize("L,k", [(8, 1), (33, 5)])
+def test_observable_l1_norms_twisted_x(orc, L, k):
+    """The L1 norms per site of the sums behind m, e and s on a twisted
+    field: every x-link has |cos| = |cos q| and |sin| = |sin q|, every y-link
+    cos = 1 and sin = 0, and the site sums average |cos|, |sin| of 2 pi k x / L
+    over the columns."""
+    th = synth.twisted_angles(L, k, axis=0)
+    o = orc.measure(th, L, L, 0.9)
+    q = 2 * math.pi * k / L
+    assert o["l1_ex"] == pytest.approx(abs(math.cos(q)), abs=2e-6)
+    assert o["l1_sx"] == pytest.approx(abs(math.sin(q)), abs=2e-6)
+    assert o["l1_ey"] == pytest.approx(1.0, abs=1e-12)
+    assert o["l1_sy"] == pytest.approx(0.0, abs=1e-12)
+    col = 2 * math.pi * k * np.arange(L) / L
+    assert o["l1_mx"] == pytest.approx(np.abs(np.cos(col)).mean(), abs=1e-6)
+    assert o["l1_my"] == pytest.approx(np.abs(np.sin(col)).mean(), abs=1e-6)
+    # a sum never exceeds its L1 norm
+    for f in ("mx", "my", "ex", "sx", "ey", "sy"):
+        assert abs(o[f]) <= o["l1_" + f] + 1e-15
+
+
 def test_observables_uniform_field(orc):
     L = 10
     th = np.full(L * L, np.float32(1.25))

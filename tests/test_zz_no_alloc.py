@@ -35,7 +35,10 @@ def _static_labels(L, right, down):
     return out.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("L", [100, 1024])
+# L = 2: the periodic wrap makes a site its own right and down neighbour's
+# neighbour twice; L <= 32: one tile column (the single-column tile geometry);
+# 17 and 100: ragged tiles; 1024: the largest size the scratch holds.
+@pytest.mark.parametrize("L", [2, 17, 32, 100, 1024])
 def test_static_labels_match_workspace_labels_twice(L):
     lat = xy.Lattice(L, 1.0, 1, tile_y=32)
     for call, density in enumerate((0.55, 0.45)):
@@ -43,6 +46,37 @@ def test_static_labels_match_workspace_labels_twice(L):
         want = lat.label_bonds(right, down)
         got = _static_labels(L, right, down)
         np.testing.assert_array_equal(got, want)
+
+
+def test_static_bond_bytes_above_one_are_active():
+    """The static entry point takes any nonzero byte as an active bond; the
+    workspace path takes 0 / 1 only, so it labels the 0 / 1 version."""
+    L = 100
+    lat = xy.Lattice(L, 1.0, 1, tile_y=32)
+    right, down = synth.bond_masks(L, L, 0.5, seed=9100)
+    want = lat.label_bonds(right, down)
+    rng = np.random.default_rng(9101)
+    big_r = right * rng.choice(np.array([1, 2, 255], np.uint8), size=right.size)
+    big_d = down * rng.choice(np.array([1, 2, 255], np.uint8), size=down.size)
+    assert (big_r > 1).any() and (big_d > 1).any()
+    np.testing.assert_array_equal(_static_labels(L, big_r, big_d), want)
+
+
+def test_static_async_on_a_side_stream():
+    """sync = 0 on a stream of its own: the call only enqueues; after the
+    caller synchronises that stream the labels are complete."""
+    L = 256
+    lat = xy.Lattice(L, 1.0, 1, tile_y=32)
+    right, down = synth.bond_masks(L, L, 0.5, seed=9200)
+    want = lat.label_bonds(right, down)
+    r = torch.from_numpy(right).cuda()
+    d = torch.from_numpy(down).cuda()
+    out = torch.full((L * L,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    xy.xy_label_bonds_static(L, r.data_ptr(), d.data_ptr(), out.data_ptr(), side.cuda_stream, 0)
+    side.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), want)
 
 
 def test_static_labels_reject_sizes_beyond_the_scratch():
