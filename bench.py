@@ -48,12 +48,11 @@ M_ALG = 4.0 + 4.0 + 4.0 + 0.25 + 0.25
 M_CANON = M_ALG + 4.0
 ALG_SHARE = {"bond_label": 4.0 + 0.25, "flip_measure": 4.0 + 4.0 + 0.25}
 # Bytes the built pipeline moves per site (its own intermediates included):
-# bond + label kernel: angles in, 16-bit tile labels out, bond planes, coin
-# bits, boundary slots (key and parent, 2 x 0.375 at TY = 64); compress
-# ~0.25 (an upper figure; its slot tables stay in L2); flip kernel: tile
+# bond + label kernel: angles in, tile labels out, bond planes, coin bits,
+# tile edge table; merge and compress ~0.5 each (upper figures); flip kernel:
 # labels in, angles in and out.
-BUILT_SHARE = {"bond_label": 4.0 + 2.0 + 0.25 + 0.125 + 0.75, "flip_measure": 2.0 + 4.0 + 4.0}
-M_BUILT = BUILT_SHARE["bond_label"] + 0.25 + BUILT_SHARE["flip_measure"]
+BUILT_SHARE = {"bond_label": 4.0 + 4.0 + 0.25 + 0.125 + 0.375, "flip_measure": 12.0}
+M_BUILT = BUILT_SHARE["bond_label"] + 0.5 + 0.5 + BUILT_SHARE["flip_measure"]
 
 
 def _sm_max_mhz():

@@ -274,10 +274,8 @@ xy_status xy_run_host_async(xy_lattice *h, const void *host_angles_in,
 xy_status xy_sync(xy_lattice *h);
 
 /* ---- kernel timing ------------------------------------------------------- */
-/* Kernel index of xy_kernel_times: 0 bonds + tile labels (the cross-tile
- * merge runs inside it), 2 compress, 3 flip + measure (the finalize -- FP64
- * observables, record, PCC, next axis -- runs inside it).  Entries 1 and 4
- * stay zero (the merge and the finalize have no launches of their own). */
+/* Kernel index of xy_kernel_times: 0 bond+tile label, 1 edge merge,
+ * 2 compress, 3 flip+measure, 4 finalize. */
 #define XY_NUM_KERNELS 5
 typedef struct {
   double ms[XY_NUM_KERNELS];          /* summed device time (CUDA events)  */
@@ -339,7 +337,7 @@ xy_status xy_engine_destroy(xy_engine *e);
  * active, same meaning as xy_get_bonds) of an L x L periodic lattice into
  * d_labels (device array of L*L uint32: minimum site index of each cluster),
  * with the same kernels as xy_label_bonds.  Its scratch is a fixed array
- * built into the library (about 3.8 MB on every GPU that loads it, kept
+ * built into the library (about 1.05 MB on every GPU that loads it, kept
  * until the process exits); it calls no cudaMalloc/cudaFree.
  *   - L is limited to 2..XY_STATIC_MAX_L; larger L returns XY_EINVAL.
  *   - The first call on a device looks up the scratch's device address

@@ -58,11 +58,9 @@ EXPORTS = (
     "xy_engine_step", "xy_engine_measure", "xy_engine_get_angles", "xy_engine_get_state",
     "xy_engine_destroy",
 )
-# xy_kernel_times entries; "merge" (inside bond_label) and "finalize" (inside
-# flip_measure) have no launches of their own and stay zero
 KERNEL_NAMES = ("bond_label", "merge", "compress", "flip_measure", "finalize")
 # kernel launches of one single-lattice sweep (xy_sweep adds one per call)
-LAUNCHES_PER_SWEEP = 3
+LAUNCHES_PER_SWEEP = 5
 
 
 class XyError(RuntimeError):

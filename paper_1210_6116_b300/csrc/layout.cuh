@@ -49,9 +49,9 @@ inline bool tile_ok(uint32_t ty) { return ty == 16 || ty == 32 || ty == 64 || ty
 struct Layout {
   uint32_t L, TY, ntx, nty, ntiles, rec_cap;
   size_t esize;
-  size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0, off_theta1, off_label,
-      off_lab16, off_rplane, off_dplane, off_slot_key, off_slot_parent, off_edge_cnt, off_links,
-      off_link_count, off_coin, off_wave, total;
+  size_t off_state, off_desc, off_prefix, off_acc, off_rec, off_theta0,
+      off_theta1, off_label, off_rplane, off_dplane, off_edge, off_links, off_link_count, off_coin,
+      off_wave, total;
 };
 
 inline xy_status make_layout(const xy_config *c, Layout *lo) {
@@ -91,15 +91,11 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
   lo->off_rec = take(sizeof(ObsRecord) * lo->rec_cap);
   lo->off_theta0 = take(n * lo->esize);
   lo->off_theta1 = take(n * lo->esize);
-  const size_t slots = static_cast<size_t>(lo->ntiles) * (2 * ty + 64);  // boundary slots
   lo->off_label = take(n * sizeof(uint32_t));
-  lo->off_lab16 = take(n * sizeof(uint16_t));
   lo->off_rplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
   lo->off_dplane = take(static_cast<size_t>(lo->ntiles) * ty * sizeof(uint32_t));
-  lo->off_slot_key = take(slots * sizeof(uint32_t));
-  lo->off_slot_parent = take(slots * sizeof(uint32_t));
-  lo->off_edge_cnt = take(static_cast<size_t>(lo->ntiles) * 2 * sizeof(uint32_t));
-  lo->off_links = take(slots * sizeof(uint32_t));
+  lo->off_edge = take(static_cast<size_t>(lo->ntiles) * (2 * ty + 64) * sizeof(uint32_t));
+  lo->off_links = take(static_cast<size_t>(lo->ntiles) * (ty + 32) * sizeof(uint32_t));
   lo->off_link_count = take(static_cast<size_t>(lo->ntiles) * sizeof(uint32_t));
   lo->off_coin = take((n / 32 + 2) * sizeof(uint32_t));
   lo->off_wave = take(static_cast<size_t>(c->L) * 8);
@@ -107,12 +103,6 @@ inline xy_status make_layout(const xy_config *c, Layout *lo) {
   return XY_OK;
 }
 
-
-// Bytes of the per-tile edge arrival counters, which must start at zero (the
-// sweeps leave them at zero).
-inline size_t edge_cnt_bytes(const Layout &lo) {
-  return static_cast<size_t>(lo.ntiles) * 2 * sizeof(uint32_t);
-}
 
 // Device descriptor of a lattice whose workspace starts at ws.
 inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
@@ -131,12 +121,9 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.theta[0] = ws + lo.off_theta0;
   d.theta[1] = ws + lo.off_theta1;
   d.label = reinterpret_cast<uint32_t *>(ws + lo.off_label);
-  d.lab16 = reinterpret_cast<uint16_t *>(ws + lo.off_lab16);
   d.rplane = reinterpret_cast<uint32_t *>(ws + lo.off_rplane);
   d.dplane = reinterpret_cast<uint32_t *>(ws + lo.off_dplane);
-  d.slot_key = reinterpret_cast<uint32_t *>(ws + lo.off_slot_key);
-  d.slot_parent = reinterpret_cast<uint32_t *>(ws + lo.off_slot_parent);
-  d.edge_cnt = reinterpret_cast<uint32_t *>(ws + lo.off_edge_cnt);
+  d.edge = reinterpret_cast<uint32_t *>(ws + lo.off_edge);
   d.links = reinterpret_cast<uint32_t *>(ws + lo.off_links);
   d.link_count = reinterpret_cast<uint32_t *>(ws + lo.off_link_count);
   d.coin = reinterpret_cast<uint32_t *>(ws + lo.off_coin);

@@ -2,40 +2,30 @@
 // 2D XY model in Wolff's embedding (Komura & Okabe, Secs. 1-2; Eq. (3)).
 //
 // Per sweep t, on every lattice of a launch (one lattice, or a batch of
-// independent replicas that share the launch), three kernels:
+// independent replicas that share the launch):
 //   k_bond_label   projection a_i = s_i.r, right/down bonds with
 //                  p = 1 - exp(-2 beta a_i a_j), 2-bit masks (two bit planes),
-//                  cluster coin bits, union-find inside the 32 x TY tile in
-//                  shared memory, 16-bit tile-local labels, and the tile's
-//                  boundary slots (a compact union-find node per boundary
-//                  site).  The second of the two tiles that share an edge to
-//                  finish also unites the clusters across that edge (CAS
-//                  linking of slot roots, the smaller key -- minimum site
-//                  index -- wins), so the merge overlaps the labeling.
-//   k_compress     points every linked slot straight at its root and gives it
-//                  the root's key.
-//   k_flip_measure canonical label of every site (the minimum site index of
-//                  its cluster), Wolff reflection theta' = C - theta (mod 2 pi)
-//                  of clusters whose root coin is 1, and the observable sums
-//                  of Eqs. (3)-(6) in exact integer fixed point; the last
-//                  tile of a lattice to finish forms the FP64 observables, the
-//                  record, the helicity-modulus PCC step (Sec. 2) and the
-//                  random axis of the next sweep.
+//                  cluster coin bits, then union-find inside the 32 x TY tile
+//                  in shared memory; writes tile-local labels (global index of
+//                  the tile-local minimum site).
+//   k_merge        union of the tile-local clusters across tile edges in the
+//                  global label array (CAS linking, smaller index wins, so the
+//                  final root is the minimum site index of the cluster).
+//   k_compress     points every merged tile root straight at its final root.
+//   k_flip_measure canonical label of every site, Wolff reflection
+//                  theta' = C - theta (mod 2 pi) of clusters whose root coin is
+//                  1, and the observable sums of Eqs. (3)-(6) on the new
+//                  configuration, in exact integer fixed point.
+//   k_finalize     FP64 observables, the record ring, the helicity-modulus PCC
+//                  step (Sec. 2) and the random axis of the next sweep.
 //
 // Layouts (per lattice, N = L*L, i = y*L + x):
-//   theta[2]  angle double buffer (FP32, FP16 or u16); the sweep reads
-//             theta[cur] and writes theta[cur ^ 1], so halo reads never race
-//             with flips.
-//   lab16     N uint16 tile-local labels (see kSlotFlag).
-//   label     N uint32 canonical labels (stored for sweeps whose labels can
-//             be read back).
+//   theta[2]  angle double buffer (FP32 or FP16); the sweep reads theta[cur]
+//             and writes theta[cur ^ 1], so halo reads never race with flips.
+//   label     N uint32.
 //   rplane,   tile-major bond bit planes: word (tile*TY + r) holds the right
 //   dplane    (down) bonds of tile row r, bit c = column x0 + c.
 //   coin      linear bit array, bit i = coin of site i (read only for roots).
-//   slot_key, per tile S = 2 TY + 64 boundary slots [left column: TY][right
-//   slot_parent column: TY][top row: 32][bottom row: 32]: the key (global
-//             index of the tile-local root) and the union-find parent (a
-//             slot index) of every boundary site.
 //   acc       kSlots x kAccStride int64 accumulators of the fixed-point sums.
 #pragma once
 
@@ -56,14 +46,6 @@ constexpr int kFlipSlot = 15;          // slot entry counting the reflected site
 // default bound on the iterations of any global find / union / jump loop
 // (LatDesc::find_cap; a test may lower it to make the bound run out)
 constexpr uint32_t kFindCap = 1u << 22;
-
-// Tile-local label of a site (lab16).  Bit 15 set: the site's tile-local
-// component touches the tile boundary, and bits 0..14 are its
-// representative slot (the smallest boundary slot of the component), whose
-// union-find node resolves the cluster across tiles.  Bit 15 clear: the
-// component lies inside the tile, it is a whole cluster, and bits 0..11 are
-// its tile-local root r*32 + c (its smallest site).
-constexpr uint32_t kSlotFlag = 0x8000u;
 
 // error bits recorded in DevState::err
 constexpr uint32_t kErrFindCap = 1u;
@@ -103,7 +85,6 @@ struct DevState {
   unsigned long long n_fp64, n_fp32_wrong;
   uint32_t err;
   uint32_t seed_site;  // Wolff update t: the site whose cluster is reflected
-  uint32_t tiles_done;  // flip kernel: tiles finished this sweep (the last finalizes)
 };
 
 struct LatDesc {
@@ -117,14 +98,11 @@ struct LatDesc {
   uint32_t find_cap;  // iteration bound of the global find / union / jump loops
   const float2 *wave;  // [L]: (cos, sin)(2 pi x / L), used when xi
   void *theta[2];
-  uint32_t *label;     // canonical labels (min site index of the cluster)
-  uint16_t *lab16;     // tile-local labels (kSlotFlag)
+  uint32_t *label;
   uint32_t *rplane, *dplane;
-  uint32_t *slot_key;     // per tile S slots: global index of the slot's tile-local root
-  uint32_t *slot_parent;  // per tile S slots: union-find parent (a slot index)
-  uint32_t *edge_cnt;     // per tile: arrivals at its right [0] and bottom [1] edge
-  uint32_t *links;        // per tile S entries: the slot roots its merges linked
-  uint32_t *link_count;   // per tile: the entries used this sweep (reset by K1)
+  uint32_t *edge;  // per tile: labels of its left/right columns, top/bottom rows
+  uint32_t *links;       // per tile, TY + 32 slots: tile roots its edge items linked
+  uint32_t *link_count;  // per tile: the slots used this sweep (reset by K1)
   uint32_t *coin;
   long long *acc;
   DevState *st;
@@ -380,55 +358,50 @@ __device__ __forceinline__ void sunion(uint32_t *par, uint32_t a, uint32_t b) {
 }
 
 // ---------------------------------------------------------------------------
-// union-find over the boundary slots of all tiles (slot_parent, slot_key)
+// global union-find on site indices (label array)
 // ---------------------------------------------------------------------------
-// Every slot starts at its component's representative slot (a root).  Roots
-// are linked under the root of smaller key, so the final root of a cluster
-// carries the minimum key, i.e. the minimum site index of the cluster.  The
-// arrays are written by other CTAs of the same launch: all accesses go to L2
-// (ld.cg / st.cg / atomics).
-
-// find with path halving
-__device__ __forceinline__ uint32_t cfind(uint32_t *P, uint32_t a, DevState *st, uint32_t cap) {
+// find with path halving; only used while no other kernel reads labels
+__device__ __forceinline__ uint32_t gfind_halve(uint32_t *lab, uint32_t a,
+                                                DevState *st, uint32_t cap) {
   for (uint32_t it = 0; it < cap; ++it) {
-    const uint32_t p = __ldcg(P + a);
+    const uint32_t p = __ldcg(lab + a);
     if (p == a) return a;
-    const uint32_t gp = __ldcg(P + p);
-    if (gp != p) __stcg(P + a, gp);  // gp is an ancestor: safe to skip p
+    const uint32_t gp = __ldcg(lab + p);
+    if (gp != p) __stcg(lab + a, gp);  // gp is an ancestor: safe to skip p
     a = gp;
   }
   atomicOr(&st->err, kErrFindCap);
   return a;
 }
 
-// Union of the clusters of slots a and b.  A successful link of root x is
-// appended to the calling tile's link list (at most one per call, so the
-// items a tile merges bound its entries): k_compress jumps exactly those.
-__device__ __forceinline__ void cunion(uint32_t *P, const uint32_t *K, uint32_t a, uint32_t b,
+// A successful link of root a is appended to the calling tile's link slots
+// (at most one per call, so the tile's edge-item count bounds them; one
+// counter per tile keeps the appends from piling onto one address):
+// k_compress jumps exactly those roots.
+__device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
                                        DevState *st, uint32_t fcap, uint32_t *links,
                                        uint32_t *count, uint32_t cap) {
-  a = cfind(P, a, st, fcap);
-  b = cfind(P, b, st, fcap);
+  a = gfind_halve(lab, a, st, fcap);
+  b = gfind_halve(lab, b, st, fcap);
   for (uint32_t it = 0; a != b; ++it) {
     if (it >= fcap) {
       atomicOr(&st->err, kErrUnionCap);
       return;
     }
-    // keys of roots never change; distinct roots have distinct keys
-    if (__ldcg(K + a) < __ldcg(K + b)) {
+    if (a < b) {
       const uint32_t tmp = a;
       a = b;
       b = tmp;
     }
-    const uint32_t old = atomicCAS(P + a, a, b);  // link root a under b
+    const uint32_t old = atomicCAS(lab + a, a, b);
     if (old == a) {
       const uint32_t k = atomicAdd(count, 1u);
       if (k < cap) links[k] = a;
       else atomicOr(&st->err, kErrLinkCap);
       return;
     }
-    a = cfind(P, old, st, fcap);
-    b = cfind(P, b, st, fcap);
+    a = gfind_halve(lab, old, st, fcap);
+    b = gfind_halve(lab, b, st, fcap);
   }
 }
 
@@ -448,88 +421,13 @@ __device__ __forceinline__ void cunion(uint32_t *P, const uint32_t *K, uint32_t 
 // ---------------------------------------------------------------------------
 constexpr uint32_t kNoRoot = 0xFFFFFFFFu;
 
-// Boundary slots of a 32 x TY tile: one per site on its boundary, as
-// [left column: TY][right column: TY][top row: 32][bottom row: 32] (a corner
-// site has two).  Slot s of tile T is union-find node T * S + s.
+// Edge table of a 32 x TY tile, written by K1 and read by the merge: the
+// tile-local root (a global site index) of every site on its boundary, as
+// [left column: TY][right column: TY][top row: 32][bottom row: 32].  The
+// merge reads these compactly instead of one sector per label of a column.
 template <int TY>
-__host__ __device__ constexpr uint32_t slot_count() {
+__host__ __device__ constexpr uint32_t edge_words() {
   return 2u * TY + 64u;
-}
-
-// Tile to the right of / below tile `tile` (periodic), from its geometry.
-struct Neighbours {
-  uint32_t right, down, left, up;
-};
-
-template <int TY>
-__device__ __forceinline__ Neighbours neighbours(const LatDesc &d, const Tile &g, uint32_t tile) {
-  const uint32_t tx = g.x0 >> 5, ty = g.y0 / static_cast<uint32_t>(TY);
-  const uint32_t row = tile - tx;
-  Neighbours n;
-  n.right = row + (tx + 1u == d.ntx ? 0u : tx + 1u);
-  n.left = row + (tx == 0u ? d.ntx - 1u : tx - 1u);
-  n.down = (ty + 1u == d.nty ? 0u : ty + 1u) * d.ntx + tx;
-  n.up = (ty == 0u ? d.nty - 1u : ty - 1u) * d.ntx + tx;
-  return n;
-}
-
-// Cross-tile merge, run by the CTA of the second tile to finish an edge
-// (bits of `last`: 1 this tile's right edge, 2 its bottom edge, 4 the right
-// edge of the tile to its left, 8 the bottom edge of the tile above).  Item
-// j of the slot range: j < TY row j of the first right edge, j < 2 TY row
-// j - TY of the second, then column j - 2 TY of the first bottom edge and
-// column j - 2 TY - 32 of the second.  An active bond across the edge unites
-// the two boundary slots' clusters; the items of a warp whose endpoints
-// start at the same pair of slot parents would repeat the same union, so
-// __match_any_sync lets one lane of each group do it.  Every lane of the warp
-// takes part in each round (the match needs all 32).
-template <int TY, bool FULL>
-__device__ __forceinline__ void merge_edges(const LatDesc &d, uint32_t tile, const Tile &g,
-                                            const Neighbours &nb, uint32_t last, int warp,
-                                            int lane) {
-  constexpr uint32_t S = slot_count<TY>();
-  uint32_t *P = d.slot_parent;
-  const uint32_t *K = d.slot_key;
-  uint32_t *links = d.links + static_cast<uint64_t>(tile) * S;
-  for (uint32_t base = static_cast<uint32_t>(warp) * 32u; base < S; base += kThreads) {
-    const uint32_t j = base + static_cast<uint32_t>(lane);
-    bool act = false;
-    uint64_t a = 0, b = 0;
-    if (j < S) {
-      const bool right = j < 2u * TY;
-      const uint32_t which = right ? (j < static_cast<uint32_t>(TY) ? 1u : 4u)
-                                   : (j < 2u * TY + 32u ? 2u : 8u);
-      if (last & which) {
-        // A: the tile whose right (bottom) edge this is; B: the tile across it
-        const uint32_t A = which <= 2u ? tile : (which == 4u ? nb.left : nb.up);
-        const uint32_t Bt = which == 1u ? nb.right : (which == 2u ? nb.down : tile);
-        const Tile ga = (A == tile) ? g : tile_geom<TY, FULL>(d.L, d.ntx, d.ntx_magic, A);
-        const uint64_t pa = static_cast<uint64_t>(A) * TY;
-        if (right) {
-          const uint32_t r = j & (TY - 1u);
-          if (r < ga.h) {
-            const uint32_t w = __ldcg(d.rplane + pa + r);
-            act = (w >> (ga.w - 1u)) & 1u;
-            a = static_cast<uint64_t>(A) * S + TY + r;  // A's right column, row r
-            b = static_cast<uint64_t>(Bt) * S + r;      // B's left column, row r
-          }
-        } else {
-          const uint32_t c = (j - 2u * TY) & 31u;
-          if (c < ga.w) {
-            const uint32_t w = __ldcg(d.dplane + pa + ga.h - 1u);
-            act = (w >> c) & 1u;
-            a = static_cast<uint64_t>(A) * S + 2u * TY + 32u + c;  // A's bottom row
-            b = static_cast<uint64_t>(Bt) * S + 2u * TY + c;       // B's top row
-          }
-        }
-      }
-    }
-    const uint32_t ra = act ? __ldcg(P + a) : 0u, rb = act ? __ldcg(P + b) : 0u;
-    const unsigned long long key = act ? (static_cast<unsigned long long>(ra) << 32 | rb) : ~0ull;
-    const unsigned m = __match_any_sync(0xFFFFFFFFu, key);
-    if (act && static_cast<unsigned>(lane) == static_cast<unsigned>(__ffs(m) - 1))
-      cunion(P, K, ra, rb, d.st, d.find_cap, links, d.link_count + tile, S);
-  }
 }
 
 // lanes of the run containing `lane`: [start, end]
@@ -795,145 +693,171 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
                r0 * 32u + run_start_of(~(Rb << 1), lane));
     }
     __syncthreads();
-    // local root of every site of the band
-    uint32_t lr[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      lr[k] = 0u;
-      if (static_cast<uint32_t>(k) < nb && col_ok) lr[k] = sfind(par, labs[k]);
-    }
-    __syncthreads();  // every find is done: roots' entries can be marked
-    // Each boundary slot marks its component's root entry with 0x10000 - slot
-    // (a root's entry holds its own index, < 0x1000, until marked), so the
-    // largest mark names the smallest slot: the component's representative.
+    // every site: root of its run's root as recorded by the scan; boundary
+    // sites also into the tile's edge table
+    uint32_t *edge = d.edge + static_cast<uint64_t>(tile) * edge_words<TY>();
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       if (static_cast<uint32_t>(k) >= nb) break;
       const uint32_t r = r0 + k;
       if (col_ok) {
-        uint32_t *pr = par + lr[k];
-        if (lane == 0) atomicMax(pr, 0x10000u - r);                                  // left column
-        if (static_cast<uint32_t>(lane) + 1u == g.w) atomicMax(pr, 0x10000u - (TY + r));  // right
-        if (r == 0u) atomicMax(pr, 0x10000u - (2u * TY + lane));                     // top row
-        if (r + 1u == g.h) atomicMax(pr, 0x10000u - (2u * TY + 32u + lane));         // bottom row
+        const uint32_t root = sfind(par, labs[k]);
+        const uint32_t v = (g.y0 + (root >> 5)) * L + g.x0 + (root & 31u);
+        d.label[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] = v;
+        if (lane == 0) edge[r] = v;                                      // left column
+        if (static_cast<uint32_t>(lane) + 1u == g.w) edge[TY + r] = v;  // right column
+        if (r == 0u) edge[2 * TY + lane] = v;                           // top row
+        if (r + 1u == g.h) edge[2 * TY + 32 + lane] = v;                // bottom row
       }
-    }
-    __syncthreads();
-    // tile-local labels; each boundary slot's key (global index of its
-    // tile-local root) and initial parent (its representative slot)
-    constexpr uint32_t S = slot_count<TY>();
-    const uint64_t tslot = static_cast<uint64_t>(tile) * S;
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (static_cast<uint32_t>(k) >= nb) break;
-      const uint32_t r = r0 + k;
-      if (col_ok) {
-        const uint32_t m = par[lr[k]];
-        const bool bnd = m >= 0x8000u;
-        const uint32_t rep = 0x10000u - m;  // meaningful when bnd
-        d.lab16[static_cast<uint64_t>(g.y0 + r) * L + g.x0 + lane] =
-            static_cast<uint16_t>(bnd ? (kSlotFlag | rep) : lr[k]);
-        if (bnd) {
-          const uint32_t key = (g.y0 + (lr[k] >> 5)) * L + g.x0 + (lr[k] & 31u);
-          const uint32_t pv = static_cast<uint32_t>(tslot) + rep;
-          if (lane == 0) {
-            __stcg(d.slot_key + tslot + r, key);
-            __stcg(d.slot_parent + tslot + r, pv);
-          }
-          if (static_cast<uint32_t>(lane) + 1u == g.w) {
-            __stcg(d.slot_key + tslot + TY + r, key);
-            __stcg(d.slot_parent + tslot + TY + r, pv);
-          }
-          if (r == 0u) {
-            __stcg(d.slot_key + tslot + 2u * TY + lane, key);
-            __stcg(d.slot_parent + tslot + 2u * TY + lane, pv);
-          }
-          if (r + 1u == g.h) {
-            __stcg(d.slot_key + tslot + 2u * TY + 32u + lane, key);
-            __stcg(d.slot_parent + tslot + 2u * TY + 32u + lane, pv);
-          }
-        }
-      }
-    }
-    // Publish this tile (bond planes, slots), then arrive at its four edges.
-    // An edge's second arrival merges it: both tiles' slots are complete.
-    __threadfence();
-    __syncthreads();
-    __shared__ uint32_t s_last;
-    const Neighbours nbr = neighbours<TY>(d, g, tile);
-    if (threadIdx.x == 0) {
-      uint32_t *cnt = d.edge_cnt;
-      uint32_t m = 0u;
-      const uint64_t e[4] = {2ull * tile, 2ull * tile + 1u, 2ull * nbr.left, 2ull * nbr.up + 1u};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (atomicAdd(cnt + e[q], 1u) == 1u) {
-          m |= 1u << q;
-          cnt[e[q]] = 0u;  // the edge is done for this sweep
-        }
-      }
-      // bit order of merge_edges: 1 own right, 2 own bottom, 4 left's right, 8 upper's bottom
-      s_last = m;
-    }
-    __syncthreads();
-    const uint32_t last = s_last;
-    if (last) {
-      __threadfence();  // see the other tile's published slots
-      merge_edges<TY, FULL>(d, tile, g, nbr, last, warp, lane);
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// K3: compress the slots the merges linked
+// K2: merge across tile edges.  Work item = (tile, j): j < TY is the right
+// edge of tile row j, j >= TY the bottom edge of column j - TY.
 // ---------------------------------------------------------------------------
+// Edge item j of a tile: j < TY is the bond from row j of its right column
+// to the next tile, j >= TY the bond from column j - TY of its bottom row to
+// the tile below.  Returns whether that bond exists and is active, and the
+// tile roots of its two endpoints from the edge table.  The roots are loaded
+// together with the bond's plane word (all three addresses lie inside their
+// arrays whatever the bond), so the chain of dependent loads is one shorter.
+// (Repeated unions of the same two tile roots are grouped in k_merge; a
+// check of the neighbouring bonds here saved fewer of them than its plane
+// loads cost.)
+template <int TY, bool FULL>
+__device__ __forceinline__ bool edge_roots(const LatDesc &d, uint32_t tile, uint32_t j,
+                                           uint32_t *ta, uint32_t *tb) {
+  constexpr uint32_t EW = edge_words<TY>();
+  const Tile g = tile_geom<TY, FULL>(d.L, d.ntx, d.ntx_magic, tile);
+  const uint64_t base = static_cast<uint64_t>(tile) * TY;
+  const uint32_t tx = g.x0 >> 5;
+  const uint32_t *plane;
+  uint64_t ea, eb;
+  uint32_t bit;
+  bool valid;
+  if (j < static_cast<uint32_t>(TY)) {
+    // the neighbouring tile to the right holds column xh as its column 0
+    const uint32_t tn = tile - tx + (tx + 1u == d.ntx ? 0u : tx + 1u);
+    valid = j < g.h;
+    bit = g.w - 1u;
+    plane = d.rplane + base + j;
+    ea = static_cast<uint64_t>(tile) * EW + TY + j;  // right column, row j
+    eb = static_cast<uint64_t>(tn) * EW + j;         // its left column, row j
+  } else {
+    // the tile below holds row yh as its row 0, same columns
+    const uint32_t c = j - TY;
+    const uint32_t ty = g.y0 / static_cast<uint32_t>(TY);
+    const uint32_t tb_ = (ty + 1u == d.nty ? 0u : (ty + 1u) * d.ntx) + tx;
+    valid = c < g.w;
+    bit = c;
+    plane = d.dplane + base + g.h - 1u;
+    ea = static_cast<uint64_t>(tile) * EW + 2 * TY + 32 + c;  // bottom row, column c
+    eb = static_cast<uint64_t>(tb_) * EW + 2 * TY + c;        // its top row, column c
+  }
+  const uint32_t w = __ldg(plane);
+  *ta = __ldg(d.edge + ea);
+  *tb = __ldg(d.edge + eb);
+  return valid && ((w >> bit) & 1u);
+}
+
+// The edge items of one warp (a tile edge, or parts of two for TY = 16 and
+// 128) whose endpoints have the same pair of tile roots would repeat the same
+// union; __match_any_sync on the pair (and on the lattice, as root indices
+// are per lattice) lets one lane of each group do it (merge at L = 4096:
+// 34.3 -> 29.0 us).  Lanes past the last item stay in the warp, clamped and
+// inactive, so every match sees all 32.
+struct EdgeItem {
+  const LatDesc *d;
+  uint32_t rep, tile, ta, tb;
+  bool act;
+};
+
+template <int TY, bool FULL>
+__device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
+                                              const uint32_t *__restrict__ prefix,
+                                              uint32_t nrep, uint32_t nwork) {
+  const uint64_t item = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
+  const uint64_t per = TY + 32;
+  const uint64_t total = static_cast<uint64_t>(nwork) * per;  // > 0: launches have work
+  const uint64_t it = item < total ? item : total - 1u;
+  const uint32_t work = static_cast<uint32_t>(it / per);
+  const uint32_t j = static_cast<uint32_t>(it % per);
+  EdgeItem e;
+  e.rep = find_rep(prefix, nrep, work);
+  e.d = descs + e.rep;
+  const uint32_t tile = work - __ldg(prefix + e.rep);
+  e.tile = tile;
+  const bool bond = edge_roots<TY, FULL>(*e.d, tile, j, &e.ta, &e.tb);
+  e.act = item < total && bond;
+  if (!e.act) e.ta = e.tb = 0u;
+  return e;
+}
+
+// true on the lowest lane of each group of lanes holding the same key
+__device__ __forceinline__ bool group_leader(unsigned long long key, uint32_t rep) {
+  const unsigned m = __match_any_sync(0xFFFFFFFFu, key) & __match_any_sync(0xFFFFFFFFu, rep);
+  return (threadIdx.x & 31u) == static_cast<unsigned>(__ffs(m) - 1);
+}
+
+template <int TY, bool FULL = false>
+__global__ void __launch_bounds__(kThreads)
+    k_merge(const LatDesc *__restrict__ descs,
+            const uint32_t *__restrict__ prefix, uint32_t nrep,
+            uint32_t nwork) {
+  pdl_prologue();
+  if (nwork == 0u) return;
+  // start from the tile roots (from the edge table): labels of non-root sites
+  // are never written here, so after the merge every site still points at
+  // its tile root
+  const EdgeItem e = edge_item<TY, FULL>(descs, prefix, nrep, nwork);
+  const unsigned long long key =
+      e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
+  if (group_leader(key, e.rep) && e.act)
+    gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->find_cap, e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u),
+           e.d->link_count + e.tile, TY + 32u);
+}
+
 // Pointer jumping: x re-points at its grandparent until its parent is a
-// root.  When all linked slots jump concurrently, a chain of length d
+// root.  When all linked roots jump concurrently, a chain of length d
 // collapses in O(log d) steps per node instead of a walk of length d.  Only
-// ancestors are ever written and roots no longer change.  Returns the root.
-__device__ __forceinline__ uint32_t jump(uint32_t *P, uint32_t x, DevState *st, uint32_t cap) {
+// ancestors are ever written and roots no longer change.
+__device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st, uint32_t cap) {
   for (uint32_t it = 0; it < cap; ++it) {
-    const uint32_t p = __ldcg(P + x);
-    if (p == x) return x;
-    const uint32_t gp = __ldcg(P + p);
-    if (gp == p) return p;
-    __stcg(P + x, gp);
+    const uint32_t p = __ldcg(lab + x);
+    if (p == x) return;
+    const uint32_t gp = __ldcg(lab + p);
+    if (gp == p) return;
+    __stcg(lab + x, gp);
   }
   atomicOr(&st->err, kErrFindCap);
-  return __ldcg(P + x);
 }
 
-// CTAs of k_compress for nwork tiles (one warp per tile).
-inline uint32_t compress_blocks(uint32_t nwork) {
-  return (nwork + kWarps - 1) / kWarps;
-}
-
-// One warp per tile: every slot the tile's merges linked (each was a root
-// when linked, so each is some component's representative) jumps to its
-// root and takes the root's key.  A representative that was never linked is
-// a root and keeps its own key, so afterwards the key of every
-// representative is the minimum site index of its cluster.  Roots are never
-// linked and their keys are never written here.
+// K3: every root the merge linked jumps (concurrently with the others) until
+// its parent is a root.  Every entry the merge changed is such a root's: the
+// link itself, or path halving, which only re-points nodes that already have
+// a parent.  Thread j of a tile's edge items takes the tile's j-th link.
 template <int TY>
 __global__ void __launch_bounds__(kThreads)
     k_compress(const LatDesc *__restrict__ descs,
                const uint32_t *__restrict__ prefix, uint32_t nrep,
                uint32_t nwork) {
   pdl_prologue();
-  constexpr uint32_t S = slot_count<TY>();
-  const uint32_t work = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (work >= nwork) return;
+  const uint64_t item = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
+  const uint64_t per = TY + 32;
+  if (item >= static_cast<uint64_t>(nwork) * per) return;
+  const uint32_t work = static_cast<uint32_t>(item / per);
+  const uint32_t j = static_cast<uint32_t>(item % per);
   const uint32_t rep = find_rep(prefix, nrep, work);
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
-  const uint32_t count = min(__ldcg(d.link_count + tile), S);
-  const uint64_t base = static_cast<uint64_t>(tile) * S;
-  for (uint32_t j = threadIdx.x & 31u; j < count; j += 32u) {
-    const uint32_t x = __ldcg(d.links + base + j);
-    const uint32_t r = jump(d.slot_parent, x, d.st, d.find_cap);
-    __stcg(d.slot_key + x, __ldcg(d.slot_key + r));
-  }
+  // the slot is read together with the count (it lies inside the tile's
+  // slots; past the count it holds an older sweep's entry and is not used)
+  const uint32_t count = __ldcg(d.link_count + tile);
+  const uint32_t x = __ldcg(d.links + static_cast<uint64_t>(tile) * per + j);
+  if (j < count) jump(d.label, x, d.st, d.find_cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -952,35 +876,22 @@ constexpr size_t flip_smem() {
   return 0;
 }
 
-// FP64 observables, record, PCC step and next axis of one lattice, run by
-// every thread of the CTA of its last tile (defined below).
-static __device__ __forceinline__ void finalize_lattice(const LatDesc &d);
-
-// Root (the minimum site index of the cluster) of a site of tile T (origin
-// x0, y0) from its tile-local label v: a component inside the tile is its
-// own cluster and its local root is the root; a boundary component's
-// representative slot has the root's key (k_compress).
-__device__ __forceinline__ uint32_t site_root(const LatDesc &d, uint32_t v, uint32_t T,
-                                              uint32_t x0, uint32_t y0, uint32_t S, uint32_t L) {
-  if (v & kSlotFlag) return __ldg(d.slot_key + static_cast<uint64_t>(T) * S + (v & 0x7FFFu));
-  return (y0 + (v >> 5)) * L + x0 + (v & 31u);
-}
-
 // K4 layout: as K1, warp w owns rows r0 .. r0+B-1 of the tile (lane =
 // column) and also resolves the row below its band (the next band's first
-// row, or the first row of the tile below) and, with lanes 0..B-1, the
-// column right of the tile (the first column of the tile to the right).
-// Roots come from the tile-local labels in one batched round of slot-key
-// loads (site_root).
+// row, or the row below the tile) and, with lanes 0..B-1, the column right of
+// the tile.  Roots come in two batched rounds of loads: a site's entry (its
+// tile root, or its root where this kernel already rewrote it), then that
+// entry's entry,
+// which k_compress has made the root (every merged tile root is jumped until
+// its parent is a root; an unmerged one is its own entry).
 // EXT: the extended instantiation, for lattice tables where some lattice
 // measures chik (d.xi) or runs Wolff updates (d.wolff); each lattice still
 // takes only what its own flags ask for.  The lean one does neither and
 // keeps its registers (launch bounds 5 CTAs/SM; EXT needs 4).
 // WL: also store the canonical labels (for a sweep whose labels the host may
-// read back, and always with LABELS_ONLY); otherwise leaving the store out
-// saves ~8 us per sweep at L = 4096.
-// Unless LABELS_ONLY, the last tile of each lattice to finish runs
-// finalize_lattice (FP64 observables, record, PCC, next axis).
+// read back, and always with LABELS_ONLY); otherwise the next sweep's K1
+// overwrites them, and leaving the store out saves ~8 us per sweep at
+// L = 4096.
 template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false, bool WL = true,
           bool FULL = false>
 __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
@@ -989,9 +900,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
                    uint32_t nwork) {
   pdl_prologue();
   constexpr int B = TY / kWarps;
-  constexpr uint32_t S = slot_count<TY>();
   __shared__ long long red[kWarps][EXT ? 15 : 6];  // EXT: 14 sums + flip count
-  __shared__ uint32_t s_final;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
@@ -1000,21 +909,19 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     const uint32_t tile = work - __ldg(prefix + rep);
     const uint32_t L = d.L;
     const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
-    const Neighbours nbr = neighbours<TY>(d, g, tile);
     DevState *st = d.st;
     const uint32_t cur = st->cur;
     const float c32 = st->c32;
     const AT *thin = static_cast<const AT *>(d.theta[cur]);
     AT *thout = static_cast<AT *>(d.theta[cur ^ 1u]);
     uint32_t *lab = d.label;
-    const uint16_t *lab16 = d.lab16;
     const uint32_t r0 = static_cast<uint32_t>(warp) * B;
     const uint32_t nb = r0 < g.h ? min(static_cast<uint32_t>(B), g.h - r0) : 0u;
     const bool col_ok = lane < static_cast<int>(g.w);
     const bool vc = static_cast<uint32_t>(lane) < nb;  // column xh, row r0+lane
     const uint64_t ic = static_cast<uint64_t>(g.y0 + r0 + lane) * L + g.xh;
 
-    // step 1: tile-local labels and angles of rows r0 .. r0+nb and of column xh
+    // step 1: labels and angles of rows r0 .. r0+nb and of column xh
     uint32_t l[B + 1];
     float t[B + 1];
 #pragma unroll
@@ -1024,26 +931,28 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       if (static_cast<uint32_t>(k) <= nb && col_ok) {
         const uint32_t r = r0 + k;
         const uint64_t i = static_cast<uint64_t>(r < g.h ? g.y0 + r : g.yh) * L + g.x0 + lane;
-        l[k] = __ldcs(lab16 + i);
+        l[k] = __ldcg(lab + i);
         if (!LABELS_ONLY) t[k] = load_angle(thin, i);
       }
     }
     uint32_t lc = 0u;
     float tc = 0.0f;
     if (vc) {
-      lc = __ldcs(lab16 + ic);
+      lc = __ldcg(lab + ic);
       if (!LABELS_ONLY) tc = load_angle(thin, ic);
     }
-    // step 2: roots (a row past the tile's last belongs to the tile below,
-    // the column xh to the tile on the right)
+    // step 2: the tile root's entry
+    uint32_t p[B + 1];
 #pragma unroll
-    for (int k = 0; k <= B; ++k) {
-      if (static_cast<uint32_t>(k) <= nb && col_ok) {
-        const bool own = r0 + k < g.h;
-        l[k] = site_root(d, l[k], own ? tile : nbr.down, g.x0, own ? g.y0 : g.yh, S, L);
-      }
-    }
-    if (vc) lc = site_root(d, lc, nbr.right, g.xh, g.y0, S, L);
+    for (int k = 0; k <= B; ++k)
+      p[k] = (static_cast<uint32_t>(k) <= nb && col_ok) ? __ldcg(lab + l[k]) : 0u;
+    const uint32_t pc = vc ? __ldcg(lab + lc) : 0u;
+    // after k_compress a site's entry is its tile root or its root, and a
+    // tile root's entry is itself or its root: the entry's entry is the root
+#pragma unroll
+    for (int k = 0; k <= B; ++k)
+      if (static_cast<uint32_t>(k) <= nb && col_ok) l[k] = p[k];
+    if (vc) lc = pc;
     // canonical labels of the band's own sites
     if constexpr (LABELS_ONLY || WL) {
 #pragma unroll
@@ -1054,17 +963,13 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     }
     if (LABELS_ONLY) continue;
     // step 3: which sites reflect.  SW: the coin of the site's root.
-    // Wolff: the sites of the seed site's cluster, i.e. whose root is the
-    // seed's root
+    // Wolff: the sites of the seed site's cluster, whose root is the entry's
+    // entry of the seed like any other site's (whether or not this kernel
+    // has already rewritten those entries: both reads give the root)
     uint32_t f[B + 1], fc;
     int nflip = 0;  // Wolff: reflected sites of the band (warp-uniform)
     if (EXT && d.wolff) {
-      const uint32_t s0 = st->seed_site;
-      const uint32_t sy = static_cast<uint32_t>(__umul64hi(s0, d.Lmagic));  // s0 / L
-      const uint32_t sx = s0 - sy * L;
-      const uint32_t sty = sy / static_cast<uint32_t>(TY);
-      const uint32_t r0 = site_root(d, __ldg(lab16 + s0), sty * d.ntx + (sx >> 5), sx & ~31u,
-                                    sty * static_cast<uint32_t>(TY), S, L);
+      const uint32_t r0 = __ldcg(lab + __ldcg(lab + st->seed_site));
 #pragma unroll
       for (int k = 0; k <= B; ++k)
         f[k] = (static_cast<uint32_t>(k) <= nb && col_ok && l[k] == r0) ? 1u : 0u;
@@ -1188,15 +1093,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
                   static_cast<unsigned long long>(sum));
       }
     }
-    // the last tile of the lattice to finish forms the sweep's record
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_final = atomicAdd(&st->tiles_done, 1u) + 1u == d.ntiles;
-    __syncthreads();
-    if (s_final) {
-      __threadfence();  // every tile's sums are in the accumulators
-      finalize_lattice(d);
-    }
   }
 }
 
@@ -1259,41 +1156,51 @@ __device__ inline void set_sweep_params(DevState *st, uint32_t quant, uint32_t t
   st->eps = __double2float_rn(4.0 * (2.0 * beta * dx + 3.0e-7) + 0x1p-24);
 }
 
-// Finalize, run by all threads of the CTA of a lattice's last tile.  Every
-// thread t sums entry t % 16 of four accumulator slots (coalesced loads of
-// the 64 x 16 slots, which it also zeroes); lanes l and l + 16 then hold the
-// same entry, and warp 0 adds the eight warps' partial sums, so that lane k
-// of warp 0 holds entry k summed over all slots.  One FP64 instruction then
-// converts (and one scales) all of them.  Lane 0 of warp 1 draws the axis
-// of the next sweep meanwhile.  The state is read through L2 (other CTAs of
-// the launch updated its counters), field by field where it is used.
-static __device__ __forceinline__ void finalize_lattice(const LatDesc &d) {
+// K5: one CTA of two warps per lattice.  Warp 0 reduces the accumulator
+// slots and derives the record and the PCC step; warp 1 meanwhile draws the
+// axis of the next sweep, so the two FP64 chains run on two schedulers at
+// once.  Lane k of warp 0 ends with the sum of entry k over all slots: one
+// FP64 instruction then converts (and one scales) all of them, instead of a
+// serial chain on one lane.
+constexpr int kFinalizeThreads = 64;
+
+static __global__ void __launch_bounds__(kFinalizeThreads)
+    k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
+  const uint32_t rep = blockIdx.x;
+  if (rep >= nrep) return;
+  // The kernel is a chain of dependent memory accesses (ncu: ~11 us for
+  // under a thousand instructions when each field was loaded where it was
+  // used), so everything it reads is loaded in one batch: the descriptor and
+  // the state as whole structs, then the accumulator slots beside the state.
+  const LatDesc d = descs[rep];  // static: loaded before the wait
+  pdl_prologue();
   DevState *st = d.st;
+  const DevState s0 = *st;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ Axis next;
-  __shared__ long long part[kWarps][16];
-  static_assert(kSlots * kAccStride == 4 * kThreads && kAccStride == 16,
-                "four slot rows of kThreads entries, thread t holding entry t % 16");
-  const uint32_t quant = __ldcg(&st->quant), t = __ldcg(&st->t);
-  if (warp == 1 && lane == 0) next = draw_axis(quant, t + 1u, d.key0, d.key1, d.L);
-  long long a = 0;
+  static_assert(kSlots * kAccStride == 32 * 32 && kAccStride == 16,
+                "the slots read as 32 rows of 32 entries, lane l holding entry l % 16");
+  double nb = s0.beta;  // beta of the next sweep (thread 0)
+  if (warp == 1) {
+    if (lane == 0) next = draw_axis(s0.quant, s0.t + 1u, d.key0, d.key1, d.L);
+  } else {
+    // Row i of 32 consecutive entries holds slots 2i and 2i + 1, so lane l
+    // reads entry l % 16 of slot 2i + l / 16: every load and store is
+    // coalesced (lane = slot, 128 B apart, had cost ~5.6 us per sweep).
+    long long v[32];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) a += __ldcg(d.acc + q * kThreads + threadIdx.x);
+    for (int i = 0; i < 32; ++i) v[i] = __ldcg(d.acc + i * 32 + lane);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) __stcg(d.acc + q * kThreads + threadIdx.x, 0ll);
-  a += __shfl_xor_sync(0xFFFFFFFFu, a, 16);
-  if (lane < 16) part[warp][lane] = a;
-  __syncthreads();
-  double nb = 0.0;  // beta of the next sweep (thread 0)
-  if (warp == 0) {
+    for (int i = 0; i < 32; ++i) __stcg(d.acc + i * 32 + lane, 0ll);
     long long tot = 0;  // lane k and lane k + 16: entry k summed over all slots
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) tot += part[w][lane & 15];
+    for (int i = 0; i < 32; ++i) tot += v[i];
+    tot += __shfl_xor_sync(0xFFFFFFFFu, tot, 16);
     const double x = static_cast<double>(tot) * (1.0 / kFixScale);  // S_k
     const double y = x * d.inv_n;                                     // S_k / N
     double sq = (lane >= 6 && lane < 14) ? x * x : 0.0;  // |F|^2 terms of chik
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, off);
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, off);
     const double mx = __shfl_sync(0xFFFFFFFFu, y, 0), my = __shfl_sync(0xFFFFFFFFu, y, 1);
     const double ex = __shfl_sync(0xFFFFFFFFu, y, 2), sx = __shfl_sync(0xFFFFFFFFu, y, 3);
     const double ey = __shfl_sync(0xFFFFFFFFu, y, 4), sy = __shfl_sync(0xFFFFFFFFu, y, 5);
@@ -1301,8 +1208,7 @@ static __device__ __forceinline__ void finalize_lattice(const LatDesc &d) {
     const long long nf = __shfl_sync(0xFFFFFFFFu, tot, kFlipSlot);
     if (lane == 0) {
       const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
-      const double beta = __ldcg(&st->beta);
-      const uint64_t rec_count = __ldcg(&st->rec_count);
+      const double beta = s0.beta;
       ObsRecord o;
       o.mx = mx;
       o.my = my;
@@ -1314,36 +1220,32 @@ static __device__ __forceinline__ void finalize_lattice(const LatDesc &d) {
       o.energy_per_site = -(x2 + x4) * d.inv_n;
       o.upsilon = ex - beta * n * sx * sx;  // Eq. (4), J = 1, T = 1/beta
       o.beta = beta;
-      o.sweep = t;
+      o.sweep = s0.t;
       o.chik = sq * (0.5 * d.inv_n);  // 0 unless the lattice measures xi
       o.flipped = static_cast<uint64_t>(nf);
-      d.rec[rec_count % d.rec_cap] = o;
-      st->rec_count = rec_count + 1;
-      nb = beta;
-      if (__ldcg(&st->pcc_on)) {
-        const uint32_t block = __ldcg(&st->pcc_block), halve = __ldcg(&st->pcc_halve);
-        const uint64_t k = __ldcg(&st->pcc_k);
-        double acc = __ldcg(&st->pcc_acc) + beta * o.upsilon;
-        uint32_t count = __ldcg(&st->pcc_count) + 1;
-        if (count >= block) {
-          const double mean = acc / static_cast<double>(block);
-          double db = __ldcg(&st->pcc_dbeta0);
-          if (halve) db = ldexp(db, -static_cast<int>(k / halve));
-          nb = (mean < __ldcg(&st->pcc_target)) ? beta + db : beta - db;
+      d.rec[s0.rec_count % d.rec_cap] = o;
+      st->rec_count = s0.rec_count + 1;
+      if (s0.pcc_on) {
+        double acc = s0.pcc_acc + beta * o.upsilon;
+        uint32_t count = s0.pcc_count + 1;
+        if (count >= s0.pcc_block) {
+          const double mean = acc / static_cast<double>(s0.pcc_block);
+          double db = s0.pcc_dbeta0;
+          if (s0.pcc_halve) db = ldexp(db, -static_cast<int>(s0.pcc_k / s0.pcc_halve));
+          nb = (mean < s0.pcc_target) ? beta + db : beta - db;
           acc = 0.0;
           count = 0;
         }
         st->pcc_acc = acc;
         st->pcc_count = count;
-        st->pcc_k = k + 1;
+        st->pcc_k = s0.pcc_k + 1;
       }
     }
   }
-  __syncthreads();  // the next axis from warp 1
+  __syncthreads();  // both warps: the next axis from warp 1
   if (threadIdx.x == 0) {
-    st->cur = __ldcg(&st->cur) ^ 1u;
-    st->tiles_done = 0u;
-    set_sweep_params(st, quant, t + 1u, nb, next);
+    st->cur = s0.cur ^ 1u;
+    set_sweep_params(st, s0.quant, s0.t + 1u, nb, next);
   }
 }
 
@@ -1398,7 +1300,6 @@ static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   st->n_fp64 = 0;
   st->n_fp32_wrong = 0;
   st->err = 0;
-  st->tiles_done = 0;
   set_sweep_params(st, quant, 0u, beta, draw_axis(quant, 0u, d.key0, d.key1, d.L));
 }
 

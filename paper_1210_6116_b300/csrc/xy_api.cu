@@ -1,11 +1,10 @@
 // xy_api.cu -- host side of the C ABI declared in include/xy.h.
 //
 // The library owns only the small host handle; every device byte lives in the
-// caller's workspace.  A sweep is three stream-ordered launches (bonds, tile
-// labels and the cross-tile merge; compress; flip, measurement and the
-// finalize) that read all per-sweep parameters (sweep counter, beta, axis)
-// from device state, so a sequence of sweeps needs no host round trip and
-// can be captured in a CUDA graph.
+// caller's workspace.  A sweep is five stream-ordered launches (bond+tile
+// label, merge, compress, flip+measure, finalize) that read all per-sweep
+// parameters (sweep counter, beta, axis) from device state, so a sequence of
+// sweeps needs no host round trip and can be captured in a CUDA graph.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -63,7 +62,7 @@ struct xy_lattice {
   bool write_labels = true;  // the next sweep stores canonical labels
   uint64_t reported;  // sweeps already returned by xy_measure
   int sm_count;
-  // kernel timing: 4 events per sweep bracket its 3 kernels
+  // kernel timing: 6 events per sweep bracket its 5 kernels
   uint32_t prof;       // 0: off; k: time every k-th sweep
   uint64_t prof_count;  // sweeps launched since profiling was enabled
   bool prof_this;       // the sweep being launched is timed
@@ -102,9 +101,11 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
                       dd, pre, 1u, nw)) != cudaSuccess)
     return e;
   if ((e = mark(h)) != cudaSuccess) return e;
-  if ((e = launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, dd, pre, 1u, nw)) !=
-      cudaSuccess)
-    return e;
+  const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  if ((e = launch_pdl(k_merge<TY, FULL>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
+  if ((e = mark(h)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_compress<TY>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   // the extended K4 for chik sums or Wolff; canonical labels only for the
   // last sweep of an xy_sweep / xy_pcc_step call
@@ -122,6 +123,8 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
     e = launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
                    dd, pre, 1u, nw);
   if (e != cudaSuccess) return e;
+  if ((e = mark(h)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_finalize, 1u, kFinalizeThreads, 0, s, dd, 1u)) != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -192,7 +195,10 @@ cudaError_t launch_label_only_t(xy_lattice *h) {
   cudaStream_t s = h->stream;
   k_bond_label<TY, float, true, true>
       <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
-  k_compress<TY><<<compress_blocks(nw), kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   k_flip_measure<TY, float, true>
       <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
   return cudaGetLastError();
@@ -324,8 +330,6 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
   if ((e = cudaMemsetAsync(d.coin, 0, (static_cast<size_t>(lo.L) * lo.L / 32 + 2) * 4,
                            h->stream)) != cudaSuccess)
     return bail("coin reset", e);
-  if ((e = cudaMemsetAsync(d.edge_cnt, 0, edge_cnt_bytes(lo), h->stream)) != cudaSuccess)
-    return bail("edge counter reset", e);
   k_init_state<<<1, 1, 0, h->stream>>>(d, cfg->beta, cfg->angle_dtype == XY_U16 ? 1u : 0u);
   k_init_wave<<<(lo.L + 255) / 256, 256, 0, h->stream>>>(d);
   const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;
@@ -484,15 +488,13 @@ xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out) {
   if (!h || !out) return fail(XY_EINVAL, "NULL argument");
   XY_CUDA(cudaStreamSynchronize(h->stream));
   std::memset(out, 0, sizeof(*out));
-  // events come in groups of 4 per sweep, around its 3 kernels: bond +
-  // label (+ merge), compress, flip + measure (+ finalize)
-  const int slot_of[3] = {0, 2, 3};
-  for (size_t base = 0; base + 4 <= h->ev_used; base += 4) {
-    for (int k = 0; k < 3; ++k) {
+  // events come in groups of 6 per sweep
+  for (size_t base = 0; base + 6 <= h->ev_used; base += 6) {
+    for (int k = 0; k < XY_NUM_KERNELS; ++k) {
       float ms = 0.0f;
       XY_CUDA(cudaEventElapsedTime(&ms, h->events[base + k], h->events[base + k + 1]));
-      out->ms[slot_of[k]] += ms;
-      out->launches[slot_of[k]] += 1;
+      out->ms[k] += ms;
+      out->launches[k] += 1;
     }
   }
   return XY_OK;
@@ -665,7 +667,7 @@ xy_status xy_label_bonds(xy_lattice *h, const uint8_t *host_right, const uint8_t
 xy_status xy_build_arch(int *binary_version) {
   if (!binary_version) return fail(XY_EINVAL, "binary_version is NULL");
   cudaFuncAttributes a{};
-  XY_CUDA(cudaFuncGetAttributes(&a, k_compress<64>));
+  XY_CUDA(cudaFuncGetAttributes(&a, k_finalize));
   *binary_version = a.binaryVersion;
   return XY_OK;
 }

@@ -1,10 +1,10 @@
 // xy_engine.cu -- many independent lattices stepped by shared launches.
 //
 // An engine holds a table of active lattices (slots).  One sweep of all of
-// them is the same three kernels as a single lattice, each launched once for
+// them is the same five kernels as a single lattice, each launched once for
 // the whole table: the kernels walk a tile list spanning every lattice and
 // find their lattice by a prefix search, so small lattices share the GPU
-// instead of each paying its own launches.  The three launches are captured in
+// instead of each paying its own launches.  The five launches are captured in
 // a CUDA graph, replayed once per sweep; the graph is re-captured only when
 // the active set changes (admission or retirement happens between sweeps).
 //
@@ -61,7 +61,10 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
                 bool ext, cudaStream_t s) {
   launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL>, nw, kThreads, bond_label_smem<TY>(), s, descs,
              prefix, nrep, nw);
-  launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, descs, prefix, nrep, nw);
+  const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  launch_pdl(k_merge<TY, FULL>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
+  launch_pdl(k_compress<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
     launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s, descs,
@@ -69,6 +72,7 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
   else
     launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
                descs, prefix, nrep, nw);
+  launch_pdl(k_finalize, nrep, kFinalizeThreads, 0, s, descs, nrep);
 }
 
 template <typename AT, bool EXACT, bool FULL>
@@ -245,7 +249,6 @@ xy_status xy_engine_admit(xy_engine *e, const xy_config *cfg, const xy_pcc_param
   s.desc = make_desc(&c, lo, static_cast<char *>(d_workspace));
   XY_CUDA(cudaMemsetAsync(s.desc.acc, 0, sizeof(long long) * kSlots * kAccStride, e->stream));
   XY_CUDA(cudaMemsetAsync(s.desc.coin, 0, (static_cast<size_t>(lo.L) * lo.L / 32 + 2) * 4, e->stream));
-  XY_CUDA(cudaMemsetAsync(s.desc.edge_cnt, 0, edge_cnt_bytes(lo), e->stream));
   k_init_state<<<1, 1, 0, e->stream>>>(s.desc, c.beta, c.angle_dtype == XY_U16 ? 1u : 0u);
   k_init_wave<<<(lo.L + 255) / 256, 256, 0, e->stream>>>(s.desc);
   const uint64_t n = static_cast<uint64_t>(lo.L) * lo.L;

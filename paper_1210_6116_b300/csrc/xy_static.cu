@@ -9,11 +9,10 @@
 // else comes from `g_label_scratch` below.
 //
 // The scratch array is a file-scope __device__ array, so every GPU that
-// loads this library holds it (about 3.8 MB) until the process exits.  All
+// loads this library holds it (about 1.05 MB) until the process exits.  All
 // calls share it and it keeps the contents of the last call: every call
-// rewrites the parts it reads (descriptor, state word, bit planes, edge
-// arrival counters, tile-local labels, boundary slots, link lists) before
-// using them, and calls whose work overlaps on the GPU (two streams, or two
+// rewrites the parts it reads (descriptor, state word, bit planes, tile edge
+// table, link list) before using them, and calls whose work overlaps on the GPU (two streams, or two
 // host threads at once) race on it and give wrong labels.
 #include <cuda_runtime.h>
 
@@ -33,9 +32,6 @@ constexpr uint32_t kStaticTile = 32;  // labeling tile 32 x 32
 constexpr uint32_t kStaticMaxTiles =
     (XY_STATIC_MAX_L / 32) * (XY_STATIC_MAX_L / kStaticTile);
 constexpr size_t kPlaneWords = static_cast<size_t>(kStaticMaxTiles) * kStaticTile;
-constexpr size_t kSlotWords = static_cast<size_t>(kStaticMaxTiles) * slot_count<kStaticTile>();
-
-constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // layout of the scratch array (byte offsets, each 256-aligned)
 constexpr size_t kOffDesc = 0;
@@ -43,16 +39,12 @@ constexpr size_t kOffPrefix = 256;
 constexpr size_t kOffState = 512;
 constexpr size_t kOffRplane = 1024;
 constexpr size_t kOffDplane = kOffRplane + kPlaneWords * sizeof(uint32_t);
-constexpr size_t kOffSlotKey = kOffDplane + kPlaneWords * sizeof(uint32_t);
-constexpr size_t kOffSlotParent = kOffSlotKey + kSlotWords * sizeof(uint32_t);
-constexpr size_t kOffLinks = kOffSlotParent + kSlotWords * sizeof(uint32_t);
-constexpr size_t kOffLinkCount = kOffLinks + kSlotWords * sizeof(uint32_t);
-constexpr size_t kOffEdgeCnt =
-    align256(kOffLinkCount + static_cast<size_t>(kStaticMaxTiles) * sizeof(uint32_t));
-constexpr size_t kOffLab16 =
-    align256(kOffEdgeCnt + static_cast<size_t>(kStaticMaxTiles) * 2 * sizeof(uint32_t));
-constexpr size_t kScratchBytes =
-    kOffLab16 + static_cast<size_t>(XY_STATIC_MAX_L) * XY_STATIC_MAX_L * sizeof(uint16_t);
+constexpr size_t kOffEdge = kOffDplane + kPlaneWords * sizeof(uint32_t);
+constexpr size_t kOffLinks =
+    kOffEdge + static_cast<size_t>(kStaticMaxTiles) * edge_words<kStaticTile>() * sizeof(uint32_t);
+constexpr size_t kOffLinkCount =
+    kOffLinks + static_cast<size_t>(kStaticMaxTiles) * (kStaticTile + 32) * sizeof(uint32_t);
+constexpr size_t kScratchBytes = kOffLinkCount + static_cast<size_t>(kStaticMaxTiles) * sizeof(uint32_t);
 static_assert(sizeof(LatDesc) <= 256 && sizeof(DevState) <= 512, "scratch layout");
 
 // The scratch memory.  In host code this name is only a stand-in for the
@@ -112,16 +104,12 @@ __global__ void k_static_setup(LatDesc d, LatDesc *d_desc, uint32_t *d_prefix) {
 }
 
 // Pack byte bonds into the tile-major bit planes: one warp per tile row.
-// Lane 0 of the first 2 ntiles warps also zeroes an edge arrival counter
-// (the labeling kernel expects them at zero; a call leaves them at zero, but
-// the scratch is shared and a call may have been cut short).
 __global__ void k_static_pack(const uint8_t *__restrict__ right,
                               const uint8_t *__restrict__ down, LatDesc d) {
   const uint64_t gw = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const uint64_t rows = static_cast<uint64_t>(d.ntiles) * kStaticTile;
   if (gw >= rows) return;
-  if (lane == 0 && gw < 2ull * d.ntiles) d.edge_cnt[gw] = 0u;
   const uint32_t tile = static_cast<uint32_t>(gw / kStaticTile);
   const uint32_t r = static_cast<uint32_t>(gw % kStaticTile);
   const Tile g = tile_geom<kStaticTile>(d.L, d.ntx, d.ntx_magic, tile);
@@ -165,10 +153,7 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   d.label = d_labels;
   d.rplane = reinterpret_cast<uint32_t *>(scratch + kOffRplane);
   d.dplane = reinterpret_cast<uint32_t *>(scratch + kOffDplane);
-  d.slot_key = reinterpret_cast<uint32_t *>(scratch + kOffSlotKey);
-  d.slot_parent = reinterpret_cast<uint32_t *>(scratch + kOffSlotParent);
-  d.edge_cnt = reinterpret_cast<uint32_t *>(scratch + kOffEdgeCnt);
-  d.lab16 = reinterpret_cast<uint16_t *>(scratch + kOffLab16);
+  d.edge = reinterpret_cast<uint32_t *>(scratch + kOffEdge);
   d.links = reinterpret_cast<uint32_t *>(scratch + kOffLinks);
   d.link_count = reinterpret_cast<uint32_t *>(scratch + kOffLinkCount);
   d.st = reinterpret_cast<DevState *>(scratch + kOffState);
@@ -183,7 +168,10 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
                                                                                   d_down, d);
   k_bond_label<kStaticTile, float, true, true>
       <<<nw, kThreads, bond_label_smem<kStaticTile>(), stream>>>(d_desc, d_prefix, 1, nw);
-  k_compress<kStaticTile><<<compress_blocks(nw), kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
+  const uint64_t items = static_cast<uint64_t>(nw) * (kStaticTile + 32);
+  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
+  k_merge<kStaticTile><<<eb, kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
+  k_compress<kStaticTile><<<eb, kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
   k_flip_measure<kStaticTile, float, true>
       <<<nw, kThreads, flip_smem<kStaticTile>(), stream>>>(d_desc, d_prefix, 1, nw);
   cudaError_t e = cudaGetLastError();
