@@ -107,6 +107,8 @@ def lib(omp: bool = False):
             "orc_bonds_f32": (ctypes.c_long, [_I, _I, _I, _I, _P, _D, _U64, _U32, _P, _P]),
             "orc_bonds_f16": (ctypes.c_long, [_I, _I, _I, _I, _P, _D, _U64, _U32, _P, _P]),
             "orc_bond_up_f32": (None, [_I, _I, _I, _I, _P, _D, _U64, _U32, ctypes.c_int64, _I, _P, _P]),
+            "orc_bonds_rows_f32": (ctypes.c_long, [_I, _P, ctypes.c_int64, _I, _D, _U64, _U32, _P, _P,
+                                                   _P, _P]),
             "orc_label_bfs": (ctypes.c_long, [_I, _I, _I, _I, _P, _P, _P, _P]),
             "orc_label_uf": (ctypes.c_long, [_I, _I, _I, _I, _P, _P, _P]),
             "orc_flip_f32": (ctypes.c_long, [_I, _I, _P, _P, _U64, _U32, ctypes.c_float, _P]),
@@ -266,9 +268,32 @@ def flip(theta: np.ndarray, label: np.ndarray, Lx: int, Ly: int, seed: int, t: i
     return fl
 
 
-def sums(theta: np.ndarray, Lx: int, Ly: int, per_x: int = 1, per_y: int = 1) -> Sums:
+def bonds_rows(theta_rows: np.ndarray, L: int, y0: int, nrows: int, beta: float, seed: int,
+               t: int):
+    """Bonds of rows y0 .. y0+nrows-1 of the L x L periodic lattice of sweep t
+    from the FP32 angles of rows y0 .. y0+nrows ((nrows + 1) x L); returns
+    (right, down, gap_right, gap_down): nrows x L bonds each, and u - p of
+    each bond."""
+    th = np.ascontiguousarray(theta_rows, np.float32)
+    assert th.size == (nrows + 1) * L
+    right = np.zeros(nrows * L, np.uint8)
+    down = np.zeros(nrows * L, np.uint8)
+    gr = np.zeros(nrows * L, np.float64)
+    gd = np.zeros(nrows * L, np.float64)
+    lib().orc_bonds_rows_f32(L, _ptr(th), y0, nrows, beta, seed, t, _ptr(right), _ptr(down),
+                             _ptr(gr), _ptr(gd))
+    return right, down, gr, gd
+
+
+def sums(theta: np.ndarray, Lx: int, Ly: int, per_x: int = 1, per_y: int = 1,
+         omp: bool = False) -> Sums:
+    """Observable sums of a configuration; omp=True runs the OpenMP build
+    (FP32 angles), which adds the same terms in another order."""
     s = Sums()
-    if theta.dtype == np.float32:
+    if omp:
+        assert theta.dtype == np.float32
+        lib(omp=True).orc_sums_f32(Lx, Ly, per_x, per_y, _ptr(theta), ctypes.byref(s))
+    elif theta.dtype == np.float32:
         lib().orc_sums_f32(Lx, Ly, per_x, per_y, _ptr(theta), ctypes.byref(s))
     elif theta.dtype == np.uint16:
         lib().orc_sums_u16(Lx, Ly, per_x, per_y, _ptr(theta), ctypes.byref(s))

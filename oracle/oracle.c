@@ -384,6 +384,41 @@ void orc_bond_up_u16(int Lx, int Ly, int per_x, int per_y, const uint16_t *q,
                   seed, t, i, dir, u, p);
 }
 
+/* Bonds of rows y0 .. y0 + nrows - 1 (mod L) of an L x L periodic lattice
+ * from the FP32 angles of rows y0 .. y0 + nrows only (theta_rows, row-major,
+ * (nrows + 1) x L): the same FP64 rule, random words and axis as the
+ * whole-lattice bonds of sweep t, for checks at sizes whose full lattice
+ * does not fit in host memory.  right / down: nrows x L bytes; gap_right /
+ * gap_down (may be NULL): u - p of each bond.  Returns the number of bonds
+ * inside the |u - p| < 1e-12 band. */
+long orc_bonds_rows_f32(int L, const float *theta_rows, int64_t y0, int nrows,
+                        double beta, uint64_t seed, uint32_t t, uint8_t *right,
+                        uint8_t *down, double *gap_right, double *gap_down) {
+  double ax[4];
+  float c32;
+  orc_axis(seed, t, ax, &c32);
+  long band = 0;
+  for (int r = 0; r < nrows; ++r) {
+    uint64_t y = (uint64_t)((y0 + r) % L);
+    for (int x = 0; x < L; ++x) {
+      uint32_t w_right, w_down;
+      bond_words(seed, t, L, y * (uint64_t)L + (uint64_t)x, &w_right, &w_down);
+      double ai = projection((double)theta_rows[(uint64_t)r * L + x], ax[1], ax[2]);
+      double ar = projection((double)theta_rows[(uint64_t)r * L + (x + 1) % L], ax[1], ax[2]);
+      double ad = projection((double)theta_rows[(uint64_t)(r + 1) * L + x], ax[1], ax[2]);
+      double pr = bond_probability(ai, ar, beta), pd = bond_probability(ai, ad, beta);
+      double ur = uniform_open(w_right), ud = uniform_open(w_down);
+      right[(uint64_t)r * L + x] = (ai * ar > 0.0) && (ur < pr);
+      down[(uint64_t)r * L + x] = (ai * ad > 0.0) && (ud < pd);
+      if (gap_right) gap_right[(uint64_t)r * L + x] = ur - pr;
+      if (gap_down) gap_down[(uint64_t)r * L + x] = ud - pd;
+      if (ai * ar > 0.0 && fabs(ur - pr) < 1e-12) ++band;
+      if (ai * ad > 0.0 && fabs(ud - pd) < 1e-12) ++band;
+    }
+  }
+  return band;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Step 3: connected components.  Label = minimum site index.                */
 /* ------------------------------------------------------------------------ */

@@ -151,6 +151,16 @@ long orc_label_bfs(int Lx, int Ly, int per_x, int per_y, const uint8_t *right,
 long orc_label_uf(int Lx, int Ly, int per_x, int per_y, const uint8_t *right,
                   const uint8_t *down, uint32_t *label);
 
+/* Bonds of rows y0 .. y0 + nrows - 1 (mod L) of an L x L periodic lattice,
+ * from the FP32 angles of rows y0 .. y0 + nrows ((nrows + 1) x L floats):
+ * identical to the whole-lattice bonds of those rows, for lattices whose
+ * full angle array is too large to widen on the host.  gap_right / gap_down
+ * (may be NULL) receive u - p of each bond.  Returns the number of bonds
+ * inside the |u - p| < 1e-12 band. */
+long orc_bonds_rows_f32(int L, const float *theta_rows, int64_t y0, int nrows,
+                        double beta, uint64_t seed, uint32_t t, uint8_t *right,
+                        uint8_t *down, double *gap_right, double *gap_down);
+
 /* Step 4: flip.  flipped[i] (optional, may be NULL) records the flip set.
  * Returns the number of flipped sites. */
 long orc_flip_f32(int Lx, int Ly, float *theta, const uint32_t *label,

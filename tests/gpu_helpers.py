@@ -102,3 +102,32 @@ def band_mismatches(orc, theta, L, beta, seed, t, g_right, g_down, o_right, o_do
             u, p = orc.bond_up(theta, L, L, beta, seed, t, int(i), direction)
             (inside if abs(u - p) < 1e-12 else outside).append((direction, int(i), u, p))
     return inside, outside
+
+
+_SUM_FIELDS = ("sum_cos", "sum_sin", "sum_cos_r", "sum_sin_r", "sum_cos_d", "sum_sin_d",
+               "abs_cos", "abs_sin", "abs_cos_r", "abs_sin_r", "abs_cos_d", "abs_sin_d")
+
+
+def banded_measure(orc, theta, L: int, beta: float, band: int = 1024, omp: bool = True) -> dict:
+    """The oracle's observables of an L x L periodic FP32 configuration,
+    computed over bands of rows so that no more than a band is widened at
+    once: each band [y0, y0 + h) is summed as an (h + 1)-row lattice, open
+    in y (its down links reach the next band's first row), minus that extra
+    row's own site and right-link terms.  Equal to orc.measure up to the
+    order of summation.  omp: the oracle's OpenMP build."""
+    tot = dict.fromkeys(_SUM_FIELDS, 0.0)
+    for y0 in range(0, L, band):
+        h = min(band, L - y0)
+        if y0 + h < L:
+            rows = theta[y0 * L:(y0 + h + 1) * L]
+        else:
+            rows = np.concatenate([theta[y0 * L:], theta[:L]])
+        s = orc.sums(rows, L, h + 1, per_x=1, per_y=0, omp=omp)
+        e = orc.sums(np.ascontiguousarray(rows[h * L:]), L, 1, per_x=1, per_y=0, omp=omp)
+        for f in _SUM_FIELDS:
+            tot[f] += getattr(s, f) - getattr(e, f)
+    s = orc.Sums()
+    for f in _SUM_FIELDS:
+        setattr(s, f, tot[f])
+    s.n_sites = s.n_links_r = s.n_links_d = float(L) * L
+    return orc.derive(s, beta)
