@@ -204,12 +204,15 @@ __device__ __forceinline__ float reflect<uint16_t>(float raw, float c) {
 // integer nearest x 2/pi, r = x - q P1 - q P2 with P1 the float nearest pi/2
 // and P2 the float nearest pi/2 - P1.  The first FMA is exact (q <= 5: the
 // difference is a multiple of 2^-24 below 1 in magnitude), the second rounds
-// once (<= 3e-8), and pi/2 - P1 - P2 = -1.8e-15 is negligible.  Then the
-// Taylor polynomials of sin to r^9 and of cos to r^10 on |r| <= pi/4
-// (truncation <= 1.8e-9), evaluated by Horner with FMAs, and the quadrant
-// q mod 4 by swapping and sign flips.  Absolute error <= 1e-7 for both (the
-// tests measure it against FP64); the SFU's __sincosf (~3.6e-7) is not
-// accurate enough for the observable tolerances.
+// once (<= 3e-8), and pi/2 - P1 - P2 = -1.8e-15 is negligible.  Then
+// minimax polynomials on |r| <= pi/4, fitted for this routine by the Remez
+// exchange algorithm (weighted absolute error, coefficients rounded to
+// FP32): sin r = r + r^3 (S0 + S1 r^2 + S2 r^4) with truncation error
+// <= 1.8e-9, cos r = 1 + r^2 (C0 + C1 r^2 + C2 r^4 + C3 r^6) with <= 5.4e-11;
+// Horner with FMAs, and the quadrant q mod 4 by swapping and sign flips.
+// Absolute error <= 1e-7 for both (the tests measure it against FP64); the
+// SFU's __sincosf (~3.6e-7) is not accurate enough for the observable
+// tolerances.
 __device__ __forceinline__ void sincos_cw(float x, float *s, float *c) {
   constexpr float kTwoOverPi = 0x1.45f306p-1f;  // float nearest 2/pi
   constexpr float kP1 = 0x1.921fb6p+0f;         // float nearest pi/2
@@ -221,14 +224,12 @@ __device__ __forceinline__ void sincos_cw(float x, float *s, float *c) {
   float r = fmaf(-q, kP1, x);
   r = fmaf(-q, kP2, r);
   const float r2 = r * r;
-  float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = fmaf(ps, r2, 1.0f / 120.0f);
-  ps = fmaf(ps, r2, -1.0f / 6.0f);
+  float ps = fmaf(r2, -0x1.98da66p-13f, 0x1.1105b4p-7f);  // S2 r^2 + S1
+  ps = fmaf(ps, r2, -0x1.55554p-3f);                      // .. + S0
   const float sr = fmaf(ps * r2, r, r);
-  float pc = fmaf(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-  pc = fmaf(pc, r2, -1.0f / 720.0f);
-  pc = fmaf(pc, r2, 1.0f / 24.0f);
-  pc = fmaf(pc, r2, -0.5f);
+  float pc = fmaf(r2, 0x1.99343p-16f, -0x1.6c087ep-10f);  // C3 r^2 + C2
+  pc = fmaf(pc, r2, 0x1.55553ep-5f);                      // .. + C1
+  pc = fmaf(pc, r2, -0.5f);                               // .. + C0
   const float cr = fmaf(pc, r2, 1.0f);
   // (sin, cos)(r + q pi/2) = (sr, cr), (cr, -sr), (-sr, -cr), (-cr, sr)
   const bool odd = (iq & 1u) != 0u;
@@ -500,11 +501,15 @@ constexpr int k1_min_blocks() {
   return (FULL && !FROM_PLANES && TY <= 64) ? 6 : 4;
 }
 
-template <int TY, typename AT, bool EXACT, bool FROM_PLANES, bool FULL = false>
+// ONE: the launch covers a single lattice whose descriptor is the kernel
+// parameter `one` (uniform constant-bank operands, the Philox key among
+// them, instead of per-thread loads of the descriptor table); otherwise
+// `one` is unused and each tile finds its lattice in `descs`.
+template <int TY, typename AT, bool EXACT, bool FROM_PLANES, bool FULL = false, bool ONE = false>
 __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANES, FULL>()))
     k_bond_label(const LatDesc *__restrict__ descs,
                  const uint32_t *__restrict__ prefix, uint32_t nrep,
-                 uint32_t nwork) {
+                 uint32_t nwork, const __grid_constant__ LatDesc one) {
   pdl_prologue();
   constexpr int B = TY / kWarps;  // rows per band
   extern __shared__ __align__(16) unsigned char smem[];
@@ -519,9 +524,9 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
   __syncwarp();
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
-    const uint32_t rep = find_rep(prefix, nrep, work);
-    const LatDesc &d = descs[rep];
-    const uint32_t tile = work - __ldg(prefix + rep);
+    const uint32_t rep = ONE ? 0u : find_rep(prefix, nrep, work);
+    const LatDesc &d = ONE ? one : descs[rep];
+    const uint32_t tile = ONE ? work : work - __ldg(prefix + rep);
     const uint32_t L = d.L;
     const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
     DevState *st = d.st;
@@ -778,8 +783,7 @@ struct EdgeItem {
 template <int TY, bool FULL>
 __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
                                               const uint32_t *__restrict__ prefix,
-                                              uint32_t nrep, uint32_t nwork) {
-  const uint64_t item = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
+                                              uint32_t nrep, uint32_t nwork, uint64_t item) {
   const uint64_t per = TY + 32;
   const uint64_t total = static_cast<uint64_t>(nwork) * per;  // > 0: launches have work
   const uint64_t it = item < total ? item : total - 1u;
@@ -802,6 +806,8 @@ __device__ __forceinline__ bool group_leader(unsigned long long key, uint32_t re
   return (threadIdx.x & 31u) == static_cast<unsigned>(__ffs(m) - 1);
 }
 
+// One thread per edge item; the loop over batches of 32 items (warp w of
+// the grid takes batches w, w + W, ...) lets any grid size cover the items.
 template <int TY, bool FULL = false>
 __global__ void __launch_bounds__(kThreads)
     k_merge(const LatDesc *__restrict__ descs,
@@ -809,15 +815,21 @@ __global__ void __launch_bounds__(kThreads)
             uint32_t nwork) {
   pdl_prologue();
   if (nwork == 0u) return;
+  const uint64_t total = static_cast<uint64_t>(nwork) * (TY + 32);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kThreads;
   // start from the tile roots (from the edge table): labels of non-root sites
   // are never written here, so after the merge every site still points at
   // its tile root
-  const EdgeItem e = edge_item<TY, FULL>(descs, prefix, nrep, nwork);
-  const unsigned long long key =
-      e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
-  if (group_leader(key, e.rep) && e.act)
-    gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->find_cap, e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u),
-           e.d->link_count + e.tile, TY + 32u);
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kThreads + (threadIdx.x & ~31u);
+       base < total; base += stride) {
+    const EdgeItem e = edge_item<TY, FULL>(descs, prefix, nrep, nwork, base + (threadIdx.x & 31u));
+    const unsigned long long key =
+        e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
+    if (group_leader(key, e.rep) && e.act)
+      gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->find_cap,
+             e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u), e.d->link_count + e.tile,
+             TY + 32u);
+  }
 }
 
 // Pointer jumping: x re-points at its grandparent until its parent is a
@@ -839,26 +851,28 @@ __device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st, ui
 // its parent is a root.  Every entry the merge changed is such a root's: the
 // link itself, or path halving, which only re-points nodes that already have
 // a parent.  Thread j of a tile's edge items takes the tile's j-th link.
+// One warp per tile (k_compress CTA b holds tiles 8b .. 8b + 7): its lanes
+// take the tile's links j = lane, lane + 32, ... below the tile's count, so
+// tiles that linked nothing cost one load.
 template <int TY>
 __global__ void __launch_bounds__(kThreads)
     k_compress(const LatDesc *__restrict__ descs,
                const uint32_t *__restrict__ prefix, uint32_t nrep,
                uint32_t nwork) {
   pdl_prologue();
-  const uint64_t item = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x;
-  const uint64_t per = TY + 32;
-  if (item >= static_cast<uint64_t>(nwork) * per) return;
-  const uint32_t work = static_cast<uint32_t>(item / per);
-  const uint32_t j = static_cast<uint32_t>(item % per);
+  const uint32_t work = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (work >= nwork) return;
   const uint32_t rep = find_rep(prefix, nrep, work);
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
-  // the slot is read together with the count (it lies inside the tile's
-  // slots; past the count it holds an older sweep's entry and is not used)
-  const uint32_t count = __ldcg(d.link_count + tile);
-  const uint32_t x = __ldcg(d.links + static_cast<uint64_t>(tile) * per + j);
-  if (j < count) jump(d.label, x, d.st, d.find_cap);
+  constexpr uint32_t per = TY + 32;
+  const uint32_t count = min(__ldcg(d.link_count + tile), per);
+  const uint32_t *links = d.links + static_cast<uint64_t>(tile) * per;
+  for (uint32_t j = threadIdx.x & 31u; j < count; j += 32u) jump(d.label, __ldcg(links + j), d.st, d.find_cap);
 }
+
+// CTAs of k_compress for nwork tiles
+inline uint32_t compress_blocks(uint32_t nwork) { return (nwork + kWarps - 1) / kWarps; }
 
 // ---------------------------------------------------------------------------
 // K4: canonical labels, flip, observable sums
@@ -893,20 +907,20 @@ constexpr size_t flip_smem() {
 // overwrites them, and leaving the store out saves ~8 us per sweep at
 // L = 4096.
 template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false, bool WL = true,
-          bool FULL = false>
+          bool FULL = false, bool ONE = false>
 __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
-                   uint32_t nwork) {
+                   uint32_t nwork, const __grid_constant__ LatDesc one) {
   pdl_prologue();
   constexpr int B = TY / kWarps;
   __shared__ long long red[kWarps][EXT ? 15 : 6];  // EXT: 14 sums + flip count
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
-    const uint32_t rep = find_rep(prefix, nrep, work);
-    const LatDesc &d = descs[rep];
-    const uint32_t tile = work - __ldg(prefix + rep);
+    const uint32_t rep = ONE ? 0u : find_rep(prefix, nrep, work);
+    const LatDesc &d = ONE ? one : descs[rep];
+    const uint32_t tile = ONE ? work : work - __ldg(prefix + rep);
     const uint32_t L = d.L;
     const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
     DevState *st = d.st;

@@ -97,31 +97,36 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   if ((e = mark(h)) != cudaSuccess) return e;
   const LatDesc *dd = h->d_desc;
   const uint32_t *pre = h->d_prefix;
-  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL>, nw, kThreads, bond_label_smem<TY>(), s,
-                      dd, pre, 1u, nw)) != cudaSuccess)
+  const LatDesc &one = h->desc;
+  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL, true>, nw, kThreads,
+                      bond_label_smem<TY>(), s, dd, pre, 1u, nw, one)) != cudaSuccess)
     return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
-  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  if ((e = launch_pdl(k_merge<TY, FULL>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
+  const uint64_t eb = (items + kThreads - 1) / kThreads;
+  if ((e = launch_pdl(k_merge<TY, FULL>, static_cast<uint32_t>(eb), kThreads, 0, s, dd, pre, 1u,
+                      nw)) != cudaSuccess)
+    return e;
   if ((e = mark(h)) != cudaSuccess) return e;
-  if ((e = launch_pdl(k_compress<TY>, eb, kThreads, 0, s, dd, pre, 1u, nw)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, dd, pre, 1u, nw)) !=
+      cudaSuccess)
+    return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   // the extended K4 for chik sums or Wolff; canonical labels only for the
   // last sweep of an xy_sweep / xy_pcc_step call
   const bool ext = h->desc.xi || h->desc.wolff;
   if (ext && h->write_labels)
-    e = launch_pdl(k_flip_measure<TY, AT, false, true, true, FULL>, nw, kThreads, flip_smem<TY>(), s,
-                   dd, pre, 1u, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, true, true, FULL, true>, nw, kThreads,
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
   else if (ext)
-    e = launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
-                   dd, pre, 1u, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL, true>, nw, kThreads,
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
   else if (h->write_labels)
-    e = launch_pdl(k_flip_measure<TY, AT, false, false, true, FULL>, nw, kThreads, flip_smem<TY>(), s,
-                   dd, pre, 1u, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, false, true, FULL, true>, nw, kThreads,
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
   else
-    e = launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
-                   dd, pre, 1u, nw);
+    e = launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL, true>, nw, kThreads,
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
   if (e != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   if ((e = launch_pdl(k_finalize, 1u, kFinalizeThreads, 0, s, dd, 1u)) != cudaSuccess) return e;
@@ -138,11 +143,11 @@ cudaError_t launch_exact_full(xy_lattice *h) {
 
 template <int TY, typename AT, bool EXACT>
 cudaError_t set_attrs_t() {
-  cudaError_t e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false>,
+  cudaError_t e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false, false, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(bond_label_smem<TY>()));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false, true>,
+  e = cudaFuncSetAttribute(k_bond_label<TY, AT, EXACT, false, true, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(bond_label_smem<TY>()));
   if (e != cudaSuccess) return e;
@@ -194,13 +199,13 @@ cudaError_t launch_label_only_t(xy_lattice *h) {
   const uint32_t nw = h->lo.ntiles;
   cudaStream_t s = h->stream;
   k_bond_label<TY, float, true, true>
-      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
   k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
-  k_compress<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  k_compress<TY><<<compress_blocks(nw), kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   k_flip_measure<TY, float, true>
-      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw);
+      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, LatDesc{});
   return cudaGetLastError();
 }
 

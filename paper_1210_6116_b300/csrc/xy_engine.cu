@@ -60,18 +60,18 @@ template <int TY, typename AT, bool EXACT, bool FULL>
 void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uint32_t nw,
                 bool ext, cudaStream_t s) {
   launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL>, nw, kThreads, bond_label_smem<TY>(), s, descs,
-             prefix, nrep, nw);
+             prefix, nrep, nw, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
-  const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  launch_pdl(k_merge<TY, FULL>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
-  launch_pdl(k_compress<TY>, eb, kThreads, 0, s, descs, prefix, nrep, nw);
+  const uint64_t eb = (items + kThreads - 1) / kThreads;
+  launch_pdl(k_merge<TY, FULL>, static_cast<uint32_t>(eb), kThreads, 0, s, descs, prefix, nrep, nw);
+  launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, descs, prefix, nrep, nw);
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
     launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s, descs,
-               prefix, nrep, nw);
+               prefix, nrep, nw, LatDesc{});
   else
     launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
-               descs, prefix, nrep, nw);
+               descs, prefix, nrep, nw, LatDesc{});
   launch_pdl(k_finalize, nrep, kFinalizeThreads, 0, s, descs, nrep);
 }
 
