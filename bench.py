@@ -579,6 +579,24 @@ def run_batched(xy, args):
         eng.close()
         del eng
         torch.cuda.empty_cache()
+    # the second reading of the size set: multiples of 64 from 64 to 2048
+    # (32 sizes, most not powers of two), FP32, the same replica count
+    table64 = synth.replica_table(args.replicas, seed=3, sizes=tuple(range(64, 2049, 64)))
+    n64 = sum(r["L"] ** 2 for r in table64)
+    ty, _ = autotune.best_tile_table(table64, dtype="f32", sweeps=3, use_cache=False)
+    eng = xy.Engine(len(table64), dtype="f32", tile_y=ty)
+    for r in table64:
+        eng.admit(eng.config(r["L"], r["beta"], r["seed"]))
+    eng.step(3)
+    t = _event_time(lambda: eng.step(args.batch_sweeps), stream)
+    out["f32_step64_sizes"] = {"sizes": "L uniform over {64, 128, 192, ..., 2048}", "tile": f"32x{ty}",
+                               "sites_per_step": n64,
+                               "replica_sweeps_per_s": round(len(table64) * args.batch_sweeps / t, 1),
+                               "updates_per_ns": round(n64 * args.batch_sweeps / (t * 1e9), 3),
+                               "ms_per_step": round(t * 1e3 / args.batch_sweeps, 4)}
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
     # per-request loop: the same replicas, one lattice at a time
     n_base = args.batch_base_sweeps
     total = 0.0

@@ -236,6 +236,14 @@ xy_status xy_label_bonds(xy_lattice *h, const uint8_t *host_right,
  * default; a test sets a tiny bound to make the bound run out on purpose.
  * Synchronising. */
 xy_status xy_set_loop_bound(xy_lattice *h, uint32_t cap);
+/* Test and diagnostics: the link slots a tile may fill in one sweep's merge
+ * (cap = 0 or above the default restores the default, TY + 32: one per
+ * edge item, which never overflows).  A smaller cap makes a dense
+ * configuration overflow on purpose: the merge records the consistency
+ * error, the launches complete, and the next synchronising call returns
+ * XY_EINTERNAL (the labels of that sweep are not meaningful).
+ * Synchronising. */
+xy_status xy_set_link_cap(xy_lattice *h, uint32_t cap);
 /* The compute capability the library's device code was built for, as
  * major * 10 + minor of the loaded kernel image (103 for sm_103a).  Needs a
  * CUDA device. */

@@ -14,12 +14,14 @@ from __future__ import annotations
 
 import ctypes
 import math
+import os
 from pathlib import Path
 
 import numpy as np
 
 _PKG = Path(__file__).resolve().parent
-LIB_PATH = _PKG / "libxy.so"
+# XY_BOUNDS_CHECK=1 selects the bounds-checked build of the library
+LIB_PATH = _PKG / ("libxy_checked.so" if os.environ.get("XY_BOUNDS_CHECK") == "1" else "libxy.so")
 
 XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_EINTERNAL, XY_EUNSUPPORTED = range(7)
 XY_F32, XY_F16, XY_U16 = 0, 1, 2
@@ -53,7 +55,8 @@ EXPORTS = (
     "xy_measure", "xy_get_state", "xy_destroy", "xy_get_angles", "xy_set_angles",
     "xy_get_bonds", "xy_get_labels", "xy_get_sites", "xy_get_spins", "xy_label_bonds", "xy_get_band_stats",
     "xy_save", "xy_load", "xy_run_host", "xy_run_host_async", "xy_sync", "xy_profile",
-    "xy_profile_read", "xy_label_bonds_static", "xy_set_loop_bound", "xy_build_arch",
+    "xy_profile_read", "xy_label_bonds_static", "xy_set_loop_bound", "xy_set_link_cap",
+    "xy_build_arch",
     "xy_engine_workspace_size", "xy_engine_create", "xy_engine_admit", "xy_engine_retire",
     "xy_engine_step", "xy_engine_measure", "xy_engine_get_angles", "xy_engine_get_state",
     "xy_engine_destroy",
@@ -139,6 +142,7 @@ def load_library() -> ctypes.CDLL:
         "xy_profile_read": (I, [P, P]),
         "xy_label_bonds_static": (I, [U32, P, P, P, P, I]),
         "xy_set_loop_bound": (I, [P, U32]),
+        "xy_set_link_cap": (I, [P, U32]),
         "xy_build_arch": (I, [P]),
         "xy_engine_workspace_size": (I, [U32, P]),
         "xy_engine_create": (I, [U32, I, I, U32, P, ctypes.c_size_t, P, P]),
@@ -334,6 +338,10 @@ class Lattice:
     def set_loop_bound(self, cap: int):
         """Bound on the device-side find/union loops (0: the default)."""
         _check(load_library().xy_set_loop_bound(self.handle, int(cap)))
+
+    def set_link_cap(self, cap: int):
+        """Link slots a tile may fill per sweep (0: the default)."""
+        _check(load_library().xy_set_link_cap(self.handle, int(cap)))
 
     def band_stats(self):
         a = ctypes.c_uint64(0)

@@ -131,6 +131,7 @@ inline LatDesc make_desc(const xy_config *cfg, const Layout &lo, char *ws) {
   d.wolff = cfg->update == XY_UPDATE_WOLFF ? 1u : 0u;
   d.wave = reinterpret_cast<const float2 *>(ws + lo.off_wave);
   d.find_cap = kFindCap;
+  d.link_cap = lo.TY + 32u;
   d.acc = reinterpret_cast<long long *>(ws + lo.off_acc);
   d.st = reinterpret_cast<DevState *>(ws + lo.off_state);
   d.rec = reinterpret_cast<ObsRecord *>(ws + lo.off_rec);

@@ -50,7 +50,21 @@ constexpr uint32_t kFindCap = 1u << 22;
 // error bits recorded in DevState::err
 constexpr uint32_t kErrFindCap = 1u;
 constexpr uint32_t kErrUnionCap = 2u;
-constexpr uint32_t kErrLinkCap = 4u;  // more links than edge items (cannot happen)
+constexpr uint32_t kErrLinkCap = 4u;  // more links than the tile's link slots
+constexpr uint32_t kErrBounds = 8u;   // bounds-checked build: a global index out of range
+
+// The bounds-checked build (compiled with -DXY_BOUNDS_CHECK) tests every
+// global index that comes from data (a label value used as an address, a
+// link read back): one at or past the array's size records kErrBounds and
+// is replaced by 0, so the access stays inside the array, the launch
+// completes and the next synchronising call returns XY_EINTERNAL.  In the
+// normal build chk() is the identity: those indices are in range by
+// construction (every label is a site index of its own lattice).
+#ifdef XY_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
 
 // Fixed-point scale of the observable sums: each FP32 term in [-1, 1] is
 // rounded to a multiple of 2^-22 and summed exactly in integers.
@@ -96,6 +110,7 @@ struct LatDesc {
   uint32_t xi;     // 1: accumulate the Fourier sums of chik
   uint32_t wolff;  // 1: Wolff single-cluster update (reflect the seed's cluster)
   uint32_t find_cap;  // iteration bound of the global find / union / jump loops
+  uint32_t link_cap;  // link slots a tile may fill per sweep (at most TY + 32)
   const float2 *wave;  // [L]: (cos, sin)(2 pi x / L), used when xi
   void *theta[2];
   uint32_t *label;
@@ -112,6 +127,16 @@ struct LatDesc {
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t chk(uint32_t i, uint64_t n, DevState *st) {
+  if constexpr (kBoundsCheck) {
+    if (i >= n) {
+      atomicOr(&st->err, kErrBounds);
+      return 0u;
+    }
+  }
+  return i;
+}
+
 __device__ __forceinline__ float two_pi_f() { return 6.2831854820251465f; }
 __device__ __forceinline__ float pi_f() { return 3.14159274101257324f; }
 
@@ -362,12 +387,12 @@ __device__ __forceinline__ void sunion(uint32_t *par, uint32_t a, uint32_t b) {
 // global union-find on site indices (label array)
 // ---------------------------------------------------------------------------
 // find with path halving; only used while no other kernel reads labels
-__device__ __forceinline__ uint32_t gfind_halve(uint32_t *lab, uint32_t a,
+__device__ __forceinline__ uint32_t gfind_halve(uint32_t *lab, uint64_t n, uint32_t a,
                                                 DevState *st, uint32_t cap) {
   for (uint32_t it = 0; it < cap; ++it) {
-    const uint32_t p = __ldcg(lab + a);
+    const uint32_t p = chk(__ldcg(lab + chk(a, n, st)), n, st);
     if (p == a) return a;
-    const uint32_t gp = __ldcg(lab + p);
+    const uint32_t gp = chk(__ldcg(lab + p), n, st);
     if (gp != p) __stcg(lab + a, gp);  // gp is an ancestor: safe to skip p
     a = gp;
   }
@@ -379,11 +404,11 @@ __device__ __forceinline__ uint32_t gfind_halve(uint32_t *lab, uint32_t a,
 // (at most one per call, so the tile's edge-item count bounds them; one
 // counter per tile keeps the appends from piling onto one address):
 // k_compress jumps exactly those roots.
-__device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
+__device__ __forceinline__ void gunion(uint32_t *lab, uint64_t n, uint32_t a, uint32_t b,
                                        DevState *st, uint32_t fcap, uint32_t *links,
                                        uint32_t *count, uint32_t cap) {
-  a = gfind_halve(lab, a, st, fcap);
-  b = gfind_halve(lab, b, st, fcap);
+  a = gfind_halve(lab, n, a, st, fcap);
+  b = gfind_halve(lab, n, b, st, fcap);
   for (uint32_t it = 0; a != b; ++it) {
     if (it >= fcap) {
       atomicOr(&st->err, kErrUnionCap);
@@ -394,15 +419,15 @@ __device__ __forceinline__ void gunion(uint32_t *lab, uint32_t a, uint32_t b,
       a = b;
       b = tmp;
     }
-    const uint32_t old = atomicCAS(lab + a, a, b);
+    const uint32_t old = atomicCAS(lab + chk(a, n, st), a, b);
     if (old == a) {
       const uint32_t k = atomicAdd(count, 1u);
       if (k < cap) links[k] = a;
       else atomicOr(&st->err, kErrLinkCap);
       return;
     }
-    a = gfind_halve(lab, old, st, fcap);
-    b = gfind_halve(lab, b, st, fcap);
+    a = gfind_halve(lab, n, old, st, fcap);
+    b = gfind_halve(lab, n, b, st, fcap);
   }
 }
 
@@ -826,9 +851,9 @@ __global__ void __launch_bounds__(kThreads)
     const unsigned long long key =
         e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
     if (group_leader(key, e.rep) && e.act)
-      gunion(e.d->label, e.ta, e.tb, e.d->st, e.d->find_cap,
+      gunion(e.d->label, static_cast<uint64_t>(e.d->L) * e.d->L, e.ta, e.tb, e.d->st, e.d->find_cap,
              e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u), e.d->link_count + e.tile,
-             TY + 32u);
+             min(e.d->link_cap, TY + 32u));
   }
 }
 
@@ -836,11 +861,13 @@ __global__ void __launch_bounds__(kThreads)
 // root.  When all linked roots jump concurrently, a chain of length d
 // collapses in O(log d) steps per node instead of a walk of length d.  Only
 // ancestors are ever written and roots no longer change.
-__device__ __forceinline__ void jump(uint32_t *lab, uint32_t x, DevState *st, uint32_t cap) {
+__device__ __forceinline__ void jump(uint32_t *lab, uint64_t n, uint32_t x, DevState *st,
+                                     uint32_t cap) {
+  x = chk(x, n, st);
   for (uint32_t it = 0; it < cap; ++it) {
-    const uint32_t p = __ldcg(lab + x);
+    const uint32_t p = chk(__ldcg(lab + x), n, st);
     if (p == x) return;
-    const uint32_t gp = __ldcg(lab + p);
+    const uint32_t gp = chk(__ldcg(lab + p), n, st);
     if (gp == p) return;
     __stcg(lab + x, gp);
   }
@@ -866,9 +893,11 @@ __global__ void __launch_bounds__(kThreads)
   const LatDesc &d = descs[rep];
   const uint32_t tile = work - __ldg(prefix + rep);
   constexpr uint32_t per = TY + 32;
-  const uint32_t count = min(__ldcg(d.link_count + tile), per);
+  const uint32_t count = min(__ldcg(d.link_count + tile), min(d.link_cap, per));
   const uint32_t *links = d.links + static_cast<uint64_t>(tile) * per;
-  for (uint32_t j = threadIdx.x & 31u; j < count; j += 32u) jump(d.label, __ldcg(links + j), d.st, d.find_cap);
+  const uint64_t n = static_cast<uint64_t>(d.L) * d.L;
+  for (uint32_t j = threadIdx.x & 31u; j < count; j += 32u)
+    jump(d.label, n, __ldcg(links + j), d.st, d.find_cap);
 }
 
 // CTAs of k_compress for nwork tiles
@@ -956,11 +985,12 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       if (!LABELS_ONLY) tc = load_angle(thin, ic);
     }
     // step 2: the tile root's entry
+    const uint64_t nsites = static_cast<uint64_t>(L) * L;
     uint32_t p[B + 1];
 #pragma unroll
     for (int k = 0; k <= B; ++k)
-      p[k] = (static_cast<uint32_t>(k) <= nb && col_ok) ? __ldcg(lab + l[k]) : 0u;
-    const uint32_t pc = vc ? __ldcg(lab + lc) : 0u;
+      p[k] = (static_cast<uint32_t>(k) <= nb && col_ok) ? chk(__ldcg(lab + chk(l[k], nsites, st)), nsites, st) : 0u;
+    const uint32_t pc = vc ? chk(__ldcg(lab + chk(lc, nsites, st)), nsites, st) : 0u;
     // after k_compress a site's entry is its tile root or its root, and a
     // tile root's entry is itself or its root: the entry's entry is the root
 #pragma unroll
@@ -983,7 +1013,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     uint32_t f[B + 1], fc;
     int nflip = 0;  // Wolff: reflected sites of the band (warp-uniform)
     if (EXT && d.wolff) {
-      const uint32_t r0 = __ldcg(lab + __ldcg(lab + st->seed_site));
+      const uint32_t r0 = __ldcg(lab + chk(__ldcg(lab + st->seed_site), nsites, st));
 #pragma unroll
       for (int k = 0; k <= B; ++k)
         f[k] = (static_cast<uint32_t>(k) <= nb && col_ok && l[k] == r0) ? 1u : 0u;

@@ -16,6 +16,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/xy.h"
 #include "layout.cuh"
 #include "sweep_kernels.cuh"
@@ -353,8 +355,16 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
   return XY_OK;
 }
 
+// NVTX range around the host work of an API call (no cost without a tool
+// attached): a profiler's timeline shows which call enqueued which kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
+  NvtxRange range("xy_sweep");
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 0u, 0.0, 0.0, 0u, 1u);
   for (uint32_t k = 0; k < n_sweeps; ++k) {
     h->write_labels = k + 1 == n_sweeps;  // labels of the call's last sweep
@@ -371,6 +381,7 @@ xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p, uint32_t n_sweeps) 
   if (p->block == 0) return fail(XY_EINVAL, "block must be >= 1");
   if (!(p->dbeta0 >= 0.0) || !std::isfinite(p->dbeta0) || !std::isfinite(p->target))
     return fail(XY_EINVAL, "dbeta0 must be finite and >= 0, target finite");
+  NvtxRange range("xy_pcc_step");
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 1u, p->target, p->dbeta0, p->halve_every,
                                     p->block);
   for (uint32_t k = 0; k < n_sweeps; ++k) {
@@ -431,6 +442,7 @@ namespace {
 xy_status run_host_enqueue(xy_lattice *h, const void *host_angles_in, uint32_t n_sweeps,
                            xy_obs *host_obs, void *host_angles_out) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
+  NvtxRange range("xy_run_host");
   const size_t ab = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
   // the angle buffer the next sweep reads is theta[cur]; cur flips once per
   // sweep, so it is known on the host from the number of sweeps enqueued
@@ -681,6 +693,15 @@ xy_status xy_set_loop_bound(xy_lattice *h, uint32_t cap) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
   XY_CUDA(cudaStreamSynchronize(h->stream));
   h->desc.find_cap = cap ? cap : kFindCap;
+  XY_CUDA(cudaMemcpy(h->d_desc, &h->desc, sizeof(LatDesc), cudaMemcpyHostToDevice));
+  return XY_OK;
+}
+
+xy_status xy_set_link_cap(xy_lattice *h, uint32_t cap) {
+  if (!h) return fail(XY_EINVAL, "handle is NULL");
+  XY_CUDA(cudaStreamSynchronize(h->stream));
+  const uint32_t full = h->lo.TY + 32u;
+  h->desc.link_cap = (cap == 0u || cap > full) ? full : cap;
   XY_CUDA(cudaMemcpy(h->d_desc, &h->desc, sizeof(LatDesc), cudaMemcpyHostToDevice));
   return XY_OK;
 }

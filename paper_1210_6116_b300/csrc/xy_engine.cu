@@ -21,6 +21,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/xy.h"
 #include "layout.cuh"
 #include "sweep_kernels.cuh"
@@ -285,7 +287,15 @@ xy_status xy_engine_step(xy_engine *e, uint32_t n_sweeps) {
     if (s != XY_OK) return s;
   }
   if (e->nrep == 0 || n_sweeps == 0) return XY_OK;
-  for (uint32_t k = 0; k < n_sweeps; ++k) XY_CUDA(cudaGraphLaunch(e->exec, e->stream));
+  nvtxRangePushA("xy_engine_step");
+  for (uint32_t k = 0; k < n_sweeps; ++k) {
+    const cudaError_t ge = cudaGraphLaunch(e->exec, e->stream);
+    if (ge != cudaSuccess) {
+      nvtxRangePop();
+      return fail(XY_ECUDA, "cudaGraphLaunch failed: %s", cudaGetErrorString(ge));
+    }
+  }
+  nvtxRangePop();
   for (uint32_t k : e->order) e->slots[k].enqueued += n_sweeps;
   return XY_OK;
 }

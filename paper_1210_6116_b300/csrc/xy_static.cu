@@ -158,6 +158,7 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
   d.link_count = reinterpret_cast<uint32_t *>(scratch + kOffLinkCount);
   d.st = reinterpret_cast<DevState *>(scratch + kOffState);
   d.find_cap = kFindCap;
+  d.link_cap = kStaticTile + 32u;
   LatDesc *d_desc = reinterpret_cast<LatDesc *>(scratch + kOffDesc);
   uint32_t *d_prefix = reinterpret_cast<uint32_t *>(scratch + kOffPrefix);
   const uint32_t nw = d.ntiles;

@@ -36,6 +36,12 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_bounds_checked_library_exports_every_declared_symbol():
+    checked = ctypes.CDLL(str(xybuild.build(checked=True)))
+    for name in _declared():
+        assert hasattr(checked, name), name
+
+
 def test_library_build_targets_sm_103a_only():
     """The build compiles device code for sm_103a and nothing else (the
     loaded image's compute capability is checked on a GPU by

@@ -137,3 +137,22 @@ def test_full_batch_sampled_replicas_equal_alone(dtype):
         np.testing.assert_array_equal(eng.measure(slots[k]), recs)
         np.testing.assert_array_equal(eng.get_angles(slots[k]).view(np.uint8), ang.view(np.uint8))
     eng.close()
+
+
+def test_step64_sizes_batch_equals_alone_and_oracle(orc):
+    """The batched workload's second size reading (multiples of 64, most not
+    powers of two), tile 32 x 64: replicas of L = 192, 320, 960 and 1984 in
+    one engine equal their alone runs bit for bit, and one of them equals
+    the oracle's chain (FP64 thresholds)."""
+    sizes = (192, 320, 960, 1984)
+    eng = xy.Engine(len(sizes), exact=True, tile_y=64)
+    slots = [eng.admit(eng.config(L, 1.05 + 0.05 * k, 900 + k)) for k, L in enumerate(sizes)]
+    eng.step(4)
+    for k, (L, s) in enumerate(zip(sizes, slots)):
+        recs, ang = _alone(L, 1.05 + 0.05 * k, 900 + k, 4, exact=True, tile_y=64)
+        np.testing.assert_array_equal(eng.measure(s), recs)
+        np.testing.assert_array_equal(eng.get_angles(s), ang)
+    th = orc.init_angles(320, 901, 0)
+    orc.sw_run(th, 320, 320, 1.1, 901, 0, 4, record=False)
+    np.testing.assert_array_equal(eng.get_angles(slots[1]), th)
+    eng.close()

@@ -82,3 +82,22 @@ def test_sweep_loop_bound_runs_out_then_recovers(orc):
         assert len(rec) == 1 and int(rec[0]["sweep"]) == 1
     finally:
         lat.close()
+
+
+def test_link_capacity_overflow_is_internal_error_then_recovers(orc):
+    """With one link slot per tile, a dense mask's merge overflows the link
+    list: the consistency error reaches the host as XY_EINTERNAL, and with
+    the default capacity restored the same handle labels exactly."""
+    L = 129
+    r, d = synth.bond_masks(L, L, 0.7, seed=4712)
+    want = orc.label_bfs(r, d, L, L)[0]
+    lat = xy.Lattice(L, 1.0, 1, tile_y=32)
+    try:
+        lat.set_link_cap(1)
+        with pytest.raises(xy.XyError) as e:
+            lat.label_bonds(r, d)
+        assert e.value.status == xy.XY_EINTERNAL
+        lat.set_link_cap(0)
+        np.testing.assert_array_equal(lat.label_bonds(r, d), want)
+    finally:
+        lat.close()
