@@ -662,10 +662,10 @@ def run_precision(xy, args):
             nb = 20
             blocks = x[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
             stats[f] = (float(blocks.mean()), float(blocks.std(ddof=1) / np.sqrt(nb)))
-        res[name] = {f: {"mean": round(m, 6), "err": round(e, 6)} for f, (m, e) in stats.items()}
+        res[name] = {f: {"mean": round(m, 8), "err": round(e, 8)} for f, (m, e) in stats.items()}
     for name in ("thr_f32", "thr_f32_f16", "thr_f32_u16"):
         res[name]["shift_vs_exact"] = {
-            f: round(res[name][f]["mean"] - res["exact_f32"][f]["mean"], 6)
+            f: round(res[name][f]["mean"] - res["exact_f32"][f]["mean"], 8)
             for f in ("energy_per_site", "m2", "beta_upsilon")}
     res["config"] = f"L={L}, beta={beta}, {n} sweeps after 200, binned errors (20 bins)"
     return res
