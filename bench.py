@@ -274,27 +274,30 @@ def run_ours(args):
             "last_energy_per_site": float(recs[-1]["energy_per_site"]) if len(recs) else None,
         }
     # end to end through the C ABI with pinned host buffers
-    e2e = run_e2e(lat, args, N)
+    e2e = run_e2e(lat, args, N, pg, ws)
     clk.stop()
     if rank == 0:
         out["clocks"] = clk.summary()
         out["e2e"] = e2e
-        if args.protocol:
+        # the single-GPU reports run at N = 1 only (under torchrun the other
+        # ranks would hold their GPUs at the final barrier meanwhile)
+        extras = ws == 1
+        if args.protocol and extras:
             out["cfg1_protocol"] = run_cfg1_protocol(xy, args)
-        if args.exact_report:
+        if args.exact_report and extras:
             out["exact_mode"] = exact_report(xy, L, beta, args)
             out["storage"] = storage_report(xy, L, beta, args)
             out["wolff"] = wolff_report(xy, L, beta, args)
             out["wolff"]["sw_reflected_sites_per_ns"] = round(0.5 * value / ws, 3)
-        if args.big and ws == 1:
+        if args.big and extras:
             out["l65536"] = run_big(xy, args)
-        if args.batched:
+        if args.batched and extras:
             out["batched"] = run_batched(xy, args)
-        if args.precision:
+        if args.precision and extras:
             out["precision"] = run_precision(xy, args)
-        if args.serving:
+        if args.serving and extras:
             out["serving"] = run_serving(xy, args)
-        if not args.no_cpu:
+        if not args.no_cpu and extras:
             out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out), flush=True)
     lat.close()
@@ -364,7 +367,7 @@ def run_cfg1_protocol(xy, args):
     return out
 
 
-def run_e2e(lat, args, N):
+def run_e2e(lat, args, N, dist=None, ws: int = 1):
     """The metric through the public API with host buffers: every step copies
     its input angles from pinned host memory, sweeps once and copies the
     sweep's record back.  Two lattices on their own streams alternate
@@ -397,13 +400,17 @@ def run_e2e(lat, args, N):
         lats[k].run_host_async(ins[k], 1, outs[k])
     for k in range(2):
         lats[k].sync()
-    dt = (time.perf_counter() - t0) / n_steps
+    elapsed = time.perf_counter() - t0
     for x in lats:
         x.close()
-    return {"value": round(N / (dt * 1e9), 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
-            "d2h_bytes_per_step": int(xy.OBS_DTYPE.itemsize), "steps": n_steps,
-            "how": "xy_run_host_async per step on two alternating lattices (own streams, at most "
-                   "two steps in flight): pinned host angles in, one sweep, the sweep's record out"}
+    # whole job: every rank ran n_steps steps of its own lattices at once;
+    # the job takes as long as the slowest rank
+    value, _ = aggregate(dist, ws, N, n_steps, elapsed, device="cuda")
+    return {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 4 * N * ws,
+            "d2h_bytes_per_step": int(xy.OBS_DTYPE.itemsize) * ws, "steps": n_steps,
+            "how": "xy_run_host_async per step on two alternating lattices per rank (own streams, "
+                   "at most two steps in flight): pinned host angles in, one sweep, the sweep's "
+                   "record out; bytes counted over all ranks"}
 
 
 def exact_report(xy, L, beta, args):
