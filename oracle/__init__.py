@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY.  The C code in ``oracle.c`` is the slow, obviously
 correct reference the CUDA library is checked against.  Only the test suite,
-``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
-this package.  It does not import the CUDA library and the CUDA library does
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg and reference
+arm (``--impl reference``, which times the oracle on the host cores) may
+import this package.  It does not import the CUDA library and the CUDA library does
 not import it; they share only the seeded input generators of ``synth``.
 
 Each wrapper below follows one step of the sweep (see ``oracle.h``):

@@ -4,7 +4,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA path, never
  * to stand in for it: only the test suite, the smoke check and the benchmark's
- * CPU-baseline leg may load it.  It shares no code, header, table or constant
+ * CPU-baseline leg and reference arm (which time it on the host cores) may
+ * load it.  It shares no code, header, table or constant
  * generator with the CUDA library; both sides implement Philox4x32-10
  * independently from its published definition (Salmon, Moraes, Dror, Shaw,
  * "Parallel random numbers: as easy as 1, 2, 3", SC'11).
