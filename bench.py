@@ -234,7 +234,8 @@ def run_ours(args):
     recs = lat.measure()
     value, t_sec = aggregate(pg, ws, N, args.steps, ms / 1e3, device="cuda")
     ms_per_step = t_sec * 1e3 / args.steps
-    launches = xy.LAUNCHES_PER_SWEEP * args.steps + math.ceil(args.steps / 1024)
+    launches = (xy.LAUNCHES_PER_SWEEP * args.steps
+                + xy.LAUNCHES_PER_CALL * math.ceil(args.steps / 1024))
 
     out = None
     if rank == 0:
@@ -457,7 +458,7 @@ def storage_report(xy, L, beta, args):
         ms = e0.elapsed_time(e1) / n
         out[dt] = {"value": round(L * L / (ms * 1e6), 3), "unit": UNIT, "ms_per_step": round(ms, 5),
                    "bytes_per_angle": {"f32": 4, "f16": 2, "u16": 2}[dt],
-                   "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in kt.items()}}
+                   "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in kt.items() if v[1]}}
         lat.close()
     return out
 

@@ -169,11 +169,16 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
                   void *cuda_stream, xy_lattice **out);
 
 /* Enqueue n_sweeps sweeps at the current beta.  Each sweep appends one
- * xy_obs record to the device ring.  Asynchronous. */
+ * xy_obs record to the device ring.  Asynchronous.  The records and the
+ * next sweep's random axis are made inside the next sweep's first kernel,
+ * and one closing kernel per call makes the last record (4 launches per
+ * sweep plus 2 per call). */
 xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps);
 
 /* Enqueue n_sweeps PCC sweeps: each sweep is followed by the PCC rule above.
- * beta lives on the device, so no host round trip happens between sweeps.
+ * beta lives on the device, so no host round trip happens between sweeps
+ * (5 launches per sweep: the record and the beta step need a kernel of
+ * their own, because the next sweep's bonds depend on them).
  * XY_EINVAL on NULL params, block = 0, or negative dbeta0. */
 xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p,
                       uint32_t n_sweeps);
@@ -283,7 +288,8 @@ xy_status xy_sync(xy_lattice *h);
 
 /* ---- kernel timing ------------------------------------------------------- */
 /* Kernel index of xy_kernel_times: 0 bond+tile label, 1 edge merge,
- * 2 compress, 3 flip+measure, 4 finalize. */
+ * 2 compress, 3 flip+measure, 4 finalize (timed only in sweeps that launch
+ * it: every PCC sweep, and the last sweep of each xy_sweep call). */
 #define XY_NUM_KERNELS 5
 typedef struct {
   double ms[XY_NUM_KERNELS];          /* summed device time (CUDA events)  */

@@ -62,8 +62,13 @@ EXPORTS = (
     "xy_engine_destroy",
 )
 KERNEL_NAMES = ("bond_label", "merge", "compress", "flip_measure", "finalize")
-# kernel launches of one single-lattice sweep (xy_sweep adds one per call)
-LAUNCHES_PER_SWEEP = 5
+# kernel launches of one single-lattice sweep: xy_sweep runs 4 per sweep
+# (its finalize step is folded into the next sweep's first kernel) plus 2 per
+# call (the PCC switch and the last record); xy_pcc_step runs 5 per sweep
+# plus 1 per call
+LAUNCHES_PER_SWEEP = 4
+LAUNCHES_PER_CALL = 2
+LAUNCHES_PER_PCC_SWEEP = 5
 
 
 class XyError(RuntimeError):

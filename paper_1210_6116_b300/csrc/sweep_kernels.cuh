@@ -17,7 +17,10 @@
 //                  1, and the observable sums of Eqs. (3)-(6) on the new
 //                  configuration, in exact integer fixed point.
 //   k_finalize     FP64 observables, the record ring, the helicity-modulus PCC
-//                  step (Sec. 2) and the random axis of the next sweep.
+//                  step (Sec. 2) and the random axis of the next sweep.  At
+//                  fixed beta a single lattice runs this work in block 0 of
+//                  the next sweep's k_bond_label instead (kCtlDraw), and
+//                  k_finalize only closes each API call with the last record.
 //
 // Layouts (per lattice, N = L*L, i = y*L + x):
 //   theta[2]  angle double buffer (FP32 or FP16); the sweep reads theta[cur]
@@ -77,16 +80,37 @@ struct ObsRecord {  // identical layout to xy_obs
   uint64_t flipped;
 };
 
-struct DevState {
-  // parameters of the next sweep
+// Parameters of one sweep: its index, the angle buffer it reads, beta and
+// the random axis r of Sec. 2 with the values derived from it.
+struct SweepParams {
   uint32_t t;      // sweep counter
-  uint32_t cur;    // theta buffer holding the current angles
+  uint32_t cur;    // theta buffer holding the angles the sweep reads
   double beta;
   double cphi, sphi;     // axis of sweep t (FP64)
   float cphi32, sphi32;  // FP32 copies
   float c32;             // reflection constant: theta' = c32 - theta (mod 2pi)
   float beta2_32;        // 2 beta in FP32
   float eps;             // half-width of the FP32 error band of exact mode
+  uint32_t seed_site;    // Wolff update t: the site whose cluster is reflected
+};
+
+// Bits of K1's `ctl` argument (single-lattice launches; 0 elsewhere).  The
+// parameters of a sweep are in p[par]; with kCtlDraw the launch has one
+// block more than tiles, and its block 0 writes the parameters of the next
+// sweep into p[par ^ 1] (no kernel of this sweep reads that slot), after,
+// with kCtlRecord, appending the record of the previous sweep, whose
+// parameters that slot still holds.  This folds k_finalize into the next
+// sweep's K1 for runs at fixed beta.
+constexpr uint32_t kCtlPar = 1u, kCtlDraw = 2u, kCtlRecord = 4u;
+// k_finalize's `mode`: 0 the full step (record, PCC, next parameters into
+// both slots); kFinRecord | par: the record of the sweep in p[par], then
+// p[par] = p[par ^ 1], so that both slots again hold the next sweep's.
+constexpr uint32_t kFinRecord = 2u;
+
+struct DevState {
+  // p[0] == p[1] between API calls; within a fixed-beta call the slots
+  // alternate by sweep parity (see kCtlDraw)
+  SweepParams p[2];
   uint32_t pcc_on;
   // helicity-modulus PCC
   uint32_t pcc_block, pcc_halve, pcc_count;
@@ -98,7 +122,6 @@ struct DevState {
   // diagnostics
   unsigned long long n_fp64, n_fp32_wrong;
   uint32_t err;
-  uint32_t seed_site;  // Wolff update t: the site whose cluster is reflected
 };
 
 struct LatDesc {
@@ -524,6 +547,158 @@ constexpr size_t bond_label_smem() {
 }
 
 // ---------------------------------------------------------------------------
+// axis of sweep t and the FP32 constants derived from it and beta
+// ---------------------------------------------------------------------------
+// The part of sweep t's parameters that does not depend on beta: the axis,
+// the reflection constant and the Wolff seed site.
+struct Axis {
+  double c, s;         // cos, sin of the axis angle (FP64)
+  float c32;           // reflection constant (u16: Cq)
+  uint32_t seed_site;  // Wolff: the site whose cluster is reflected
+};
+
+__device__ inline Axis draw_axis(uint32_t quant, uint32_t t, uint32_t k0, uint32_t k1,
+                                 uint32_t L) {
+  const Words4 w = philox4x32_10(0u, 0u, t, kDomAxis, k0, k1);
+  Axis a;
+  // seed site of a Wolff update: word 2 scaled to 0 .. N-1 (N = L^2 <= 2^32)
+  a.seed_site = static_cast<uint32_t>(
+      (static_cast<uint64_t>(w.w2) * (static_cast<uint64_t>(L) * L)) >> 32);
+  const uint64_t bits = (static_cast<uint64_t>(w.w0) << 32) | w.w1;
+  if (quant) {
+    // u16 angles: the axis on the reflection grid, phi_q = pi m / 65536 with
+    // m = phi mod pi floored to the grid, and Cq = m + 32768 (mod 65536), so
+    // that pi + 2 phi_q = Cq 2pi / 65536 and the flip is q -> Cq - q
+    const uint32_t m = static_cast<uint32_t>(bits >> 47) & 0xFFFFu;
+    sincospi(static_cast<double>(m) * 0x1p-16, &a.s, &a.c);
+    a.c32 = static_cast<float>((m + 32768u) & 0xFFFFu);
+  } else {
+    const double u = static_cast<double>(bits >> 11) * 0x1p-53;
+    const double phi = __dmul_rn(6.283185307179586, u);
+    sincos(phi, &a.s, &a.c);
+    // C = (pi + 2 phi) mod 2pi.  pi + 2 phi lies in [pi, 5pi) and both
+    // subtractions are exact (Sterbenz), so this is fmod's result exactly.
+    const double two_pi = 6.283185307179586;
+    double C = __dadd_rn(3.141592653589793, __dmul_rn(2.0, phi));
+    if (C >= 2.0 * two_pi) C = __dsub_rn(C, 2.0 * two_pi);
+    else if (C >= two_pi) C = __dsub_rn(C, two_pi);
+    a.c32 = __double2float_rn(C);
+    if (a.c32 >= two_pi_f()) a.c32 = 0.0f;
+  }
+  return a;
+}
+
+__device__ inline void set_sweep_params(SweepParams *p, uint32_t quant, uint32_t t,
+                                        uint32_t cur, double beta, const Axis &a) {
+  p->t = t;
+  p->cur = cur;
+  p->beta = beta;
+  p->cphi = a.c;
+  p->sphi = a.s;
+  p->cphi32 = __double2float_rn(a.c);
+  p->sphi32 = __double2float_rn(a.s);
+  p->c32 = a.c32;
+  p->seed_site = a.seed_site;
+  p->beta2_32 = __double2float_rn(2.0 * beta);
+  // band half-width: 4x the error bound of the FP32 evaluation of u - p;
+  // u16 adds <= 4.2e-7 per projection for the FP32 angle q 2pi_f 2^-16
+  const double dx = quant ? 3.0e-6 : 2.0e-6;
+  p->eps = __double2float_rn(4.0 * (2.0 * beta * dx + 3.0e-7) + 0x1p-24);
+}
+
+// ---------------------------------------------------------------------------
+// the per-sweep record (Eqs. (3)-(6), FP64)
+// ---------------------------------------------------------------------------
+// Called by one whole warp whose lane k holds S_k, the fixed-point sum of
+// accumulator entry k % 16 over all slots.  Lane 0 appends the record of
+// sweep t to the ring and returns it (the other lanes' return is unused).
+// k_finalize and the folded record in K1 both call this, so the two give
+// bit-identical records.
+__device__ __forceinline__ ObsRecord append_record(const LatDesc &d, DevState *st,
+                                                   long long tot, double beta, uint32_t t,
+                                                   uint64_t rec_count) {
+  const int lane = threadIdx.x & 31;
+  const double x = static_cast<double>(tot) * (1.0 / kFixScale);  // S_k
+  const double y = x * d.inv_n;                                     // S_k / N
+  double sq = (lane >= 6 && lane < 14) ? x * x : 0.0;  // |F|^2 terms of chik
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, off);
+  const double mx = __shfl_sync(0xFFFFFFFFu, y, 0), my = __shfl_sync(0xFFFFFFFFu, y, 1);
+  const double ex = __shfl_sync(0xFFFFFFFFu, y, 2), sx = __shfl_sync(0xFFFFFFFFu, y, 3);
+  const double ey = __shfl_sync(0xFFFFFFFFu, y, 4), sy = __shfl_sync(0xFFFFFFFFu, y, 5);
+  const double x2 = __shfl_sync(0xFFFFFFFFu, x, 2), x4 = __shfl_sync(0xFFFFFFFFu, x, 4);
+  const long long nf = __shfl_sync(0xFFFFFFFFu, tot, kFlipSlot);
+  ObsRecord o{};
+  if (lane == 0) {
+    const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
+    o.mx = mx;
+    o.my = my;
+    o.m2 = mx * mx + my * my;
+    o.ex = ex;
+    o.sx = sx;
+    o.ey = ey;
+    o.sy = sy;
+    o.energy_per_site = -(x2 + x4) * d.inv_n;
+    o.upsilon = ex - beta * n * sx * sx;  // Eq. (4), J = 1, T = 1/beta
+    o.beta = beta;
+    o.sweep = t;
+    o.chik = sq * (0.5 * d.inv_n);  // 0 unless the lattice measures xi
+    o.flipped = static_cast<uint64_t>(nf);
+    d.rec[rec_count % d.rec_cap] = o;
+    st->rec_count = rec_count + 1;
+  }
+  return o;
+}
+
+// Block 0 of a K1 launch with kCtlDraw (single lattice, fixed beta): the
+// work of k_finalize, moved off the sweep's critical path, in two parts that
+// run at once.  Warp kRecWarps draws the next sweep's axis and writes its
+// parameters into p[par ^ 1].  With kCtlRecord, warps 0 .. kRecWarps-1
+// reduce the accumulator slots that K4 of the previous sweep filled (K4 of
+// this sweep refills them only after this grid completes) and append that
+// sweep's record.  At fixed beta the previous sweep is t - 1 at this sweep's
+// beta, so the record reads only p[par], and the two parts share no data.
+// `part` is shared memory for kRecWarps x 16 int64.
+constexpr int kRecWarps = 4;
+
+__device__ __forceinline__ void k1_fold(const LatDesc &d, uint32_t ctl, long long *part) {
+  DevState *st = d.st;
+  const uint32_t par = ctl & kCtlPar;
+  const SweepParams &now = st->p[par];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == kRecWarps) {
+    if (lane == 0) {
+      const uint32_t quant = st->quant, t1 = now.t + 1u;
+      set_sweep_params(&st->p[par ^ 1u], quant, t1, now.cur ^ 1u, now.beta,
+                       draw_axis(quant, t1, d.key0, d.key1, d.L));
+    }
+  } else if (warp < kRecWarps && (ctl & kCtlRecord)) {
+    constexpr int kRecThreads = kRecWarps * 32;
+    static_assert(kSlots * kAccStride % kRecThreads == 0 && kRecThreads % kAccStride == 0,
+                  "thread i reads entries i, i + kRecThreads, ...: all of entry i % 16");
+    constexpr int kPer = kSlots * kAccStride / kRecThreads;
+    long long v[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) v[j] = __ldcg(d.acc + j * kRecThreads + threadIdx.x);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) __stcg(d.acc + j * kRecThreads + threadIdx.x, 0ll);
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) s += v[j];
+    s += __shfl_xor_sync(0xFFFFFFFFu, s, 16);
+    if (lane < 16) part[warp * 16 + lane] = s;
+    // named barrier 1 over the reducing warps only (the drawing warp runs on)
+    asm volatile("bar.sync 1, %0;" ::"n"(kRecThreads) : "memory");
+    if (warp == 0) {
+      long long tot = 0;
+#pragma unroll
+      for (int w = 0; w < kRecWarps; ++w) tot += part[w * 16 + (lane & 15)];
+      append_record(d, st, tot, now.beta, now.t - 1u, st->rec_count);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K1: projection + bonds + coins + tile labels
 // ---------------------------------------------------------------------------
 // CTAs per SM: the whole-tile sweep kernels fit 6 (40 registers).  With
@@ -539,15 +714,22 @@ constexpr int k1_min_blocks() {
 // ONE: the launch covers a single lattice whose descriptor is the kernel
 // parameter `one` (uniform constant-bank operands, the Philox key among
 // them, instead of per-thread loads of the descriptor table); otherwise
-// `one` is unused and each tile finds its lattice in `descs`.
+// `one` is unused and each tile finds its lattice in `descs`.  `ctl` holds
+// the kCtl* bits (single lattice only; 0 for a table of lattices).
 template <int TY, typename AT, bool EXACT, bool FROM_PLANES, bool FULL = false, bool ONE = false>
 __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANES, FULL>()))
     k_bond_label(const LatDesc *__restrict__ descs,
                  const uint32_t *__restrict__ prefix, uint32_t nrep,
-                 uint32_t nwork, const __grid_constant__ LatDesc one) {
+                 uint32_t nwork, uint32_t ctl, const __grid_constant__ LatDesc one) {
   pdl_prologue();
   constexpr int B = TY / kWarps;  // rows per band
   extern __shared__ __align__(16) unsigned char smem[];
+  // kCtlDraw: block 0 folds the finalize step, tiles start at block 1
+  const uint32_t aux = (ONE && (ctl & kCtlDraw)) ? 1u : 0u;
+  if (aux && blockIdx.x == 0) {
+    k1_fold(one, ctl, reinterpret_cast<long long *>(smem));
+    return;
+  }
   uint32_t *par = reinterpret_cast<uint32_t *>(smem);
   uint32_t *sR = par + TY * 32;
   uint32_t *sD = sR + TY;
@@ -558,13 +740,14 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
   runmin[lane] = kNoRoot;
   __syncwarp();
 
-  for (uint32_t work = blockIdx.x; work < nwork; work += gridDim.x) {
+  for (uint32_t work = blockIdx.x - aux; work < nwork; work += gridDim.x - aux) {
     const uint32_t rep = ONE ? 0u : find_rep(prefix, nrep, work);
     const LatDesc &d = ONE ? one : descs[rep];
     const uint32_t tile = ONE ? work : work - __ldg(prefix + rep);
     const uint32_t L = d.L;
     const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
     DevState *st = d.st;
+    const SweepParams &sp = st->p[ctl & kCtlPar];
     uint32_t npairs = 0u;
     const uint32_t r0 = static_cast<uint32_t>(warp) * B;
     const uint32_t nb = r0 < g.h ? min(static_cast<uint32_t>(B), g.h - r0) : 0u;
@@ -576,10 +759,10 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
     uint32_t lab_prev = kNoRoot, D_prev = 0u;
     uint32_t labs[B];
     if (!FROM_PLANES) {
-      const uint32_t t = st->t;
-      const AT *th = static_cast<const AT *>(d.theta[st->cur]);
-      const float cphi = st->cphi32, sphi = st->sphi32;
-      const float b2 = st->beta2_32, eps = st->eps;
+      const uint32_t t = sp.t;
+      const AT *th = static_cast<const AT *>(d.theta[sp.cur]);
+      const float cphi = sp.cphi32, sphi = sp.sphi32;
+      const float b2 = sp.beta2_32, eps = sp.eps;
       // angles of the band, of the row below it, and (lane k < nb) of row k
       // of the column right of the tile; all loads issued up front
       float tv[B + 1];
@@ -642,14 +825,14 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
                                        ? load_angle(th, static_cast<uint64_t>(gy) * L + g.xh)
                                        : load_angle(th, static_cast<uint64_t>(i) + 1u);
                 const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(th_r), w_r,
-                                         st->beta, st->cphi, st->sphi);
+                                         sp.beta, sp.cphi, sp.sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != br) atomicAdd(&st->n_fp32_wrong, 1ull);
                 br = e;
               }
               if (amb_d) {
                 const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(tv[k + 1]), w_d,
-                                         st->beta, st->cphi, st->sphi);
+                                         sp.beta, sp.cphi, sp.sphi);
                 atomicAdd(&st->n_fp64, 1ull);
                 if (e != bd) atomicAdd(&st->n_fp32_wrong, 1ull);
                 bd = e;
@@ -950,7 +1133,7 @@ template <int TY, typename AT, bool LABELS_ONLY, bool EXT = false, bool WL = tru
 __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     k_flip_measure(const LatDesc *__restrict__ descs,
                    const uint32_t *__restrict__ prefix, uint32_t nrep,
-                   uint32_t nwork, const __grid_constant__ LatDesc one) {
+                   uint32_t nwork, uint32_t par, const __grid_constant__ LatDesc one) {
   pdl_prologue();
   constexpr int B = TY / kWarps;
   __shared__ long long red[kWarps][EXT ? 15 : 6];  // EXT: 14 sums + flip count
@@ -963,8 +1146,9 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     const uint32_t L = d.L;
     const Tile g = tile_geom<TY, FULL>(L, d.ntx, d.ntx_magic, tile);
     DevState *st = d.st;
-    const uint32_t cur = st->cur;
-    const float c32 = st->c32;
+    const SweepParams &sp = st->p[par];  // par: the sweep's parameter slot
+    const uint32_t cur = sp.cur;
+    const float c32 = sp.c32;
     const AT *thin = static_cast<const AT *>(d.theta[cur]);
     AT *thout = static_cast<AT *>(d.theta[cur ^ 1u]);
     uint32_t *lab = d.label;
@@ -1023,7 +1207,7 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
     uint32_t f[B + 1], fc;
     int nflip = 0;  // Wolff: reflected sites of the band (warp-uniform)
     if (EXT && d.wolff) {
-      const uint32_t r0 = __ldcg(lab + chk(__ldcg(lab + st->seed_site), nsites, st));
+      const uint32_t r0 = __ldcg(lab + chk(__ldcg(lab + sp.seed_site), nsites, st));
 #pragma unroll
       for (int k = 0; k <= B; ++k)
         f[k] = (static_cast<uint32_t>(k) <= nb && col_ok && l[k] == r0) ? 1u : 0u;
@@ -1151,75 +1335,18 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
   }
 }
 
-// ---------------------------------------------------------------------------
-// axis of sweep t and the FP32 constants derived from it and beta
-// ---------------------------------------------------------------------------
-// The part of sweep t's parameters that does not depend on beta: the axis,
-// the reflection constant and the Wolff seed site.
-struct Axis {
-  double c, s;         // cos, sin of the axis angle (FP64)
-  float c32;           // reflection constant (u16: Cq)
-  uint32_t seed_site;  // Wolff: the site whose cluster is reflected
-};
-
-__device__ inline Axis draw_axis(uint32_t quant, uint32_t t, uint32_t k0, uint32_t k1,
-                                 uint32_t L) {
-  const Words4 w = philox4x32_10(0u, 0u, t, kDomAxis, k0, k1);
-  Axis a;
-  // seed site of a Wolff update: word 2 scaled to 0 .. N-1 (N = L^2 <= 2^32)
-  a.seed_site = static_cast<uint32_t>(
-      (static_cast<uint64_t>(w.w2) * (static_cast<uint64_t>(L) * L)) >> 32);
-  const uint64_t bits = (static_cast<uint64_t>(w.w0) << 32) | w.w1;
-  if (quant) {
-    // u16 angles: the axis on the reflection grid, phi_q = pi m / 65536 with
-    // m = phi mod pi floored to the grid, and Cq = m + 32768 (mod 65536), so
-    // that pi + 2 phi_q = Cq 2pi / 65536 and the flip is q -> Cq - q
-    const uint32_t m = static_cast<uint32_t>(bits >> 47) & 0xFFFFu;
-    sincospi(static_cast<double>(m) * 0x1p-16, &a.s, &a.c);
-    a.c32 = static_cast<float>((m + 32768u) & 0xFFFFu);
-  } else {
-    const double u = static_cast<double>(bits >> 11) * 0x1p-53;
-    const double phi = __dmul_rn(6.283185307179586, u);
-    sincos(phi, &a.s, &a.c);
-    // C = (pi + 2 phi) mod 2pi.  pi + 2 phi lies in [pi, 5pi) and both
-    // subtractions are exact (Sterbenz), so this is fmod's result exactly.
-    const double two_pi = 6.283185307179586;
-    double C = __dadd_rn(3.141592653589793, __dmul_rn(2.0, phi));
-    if (C >= 2.0 * two_pi) C = __dsub_rn(C, 2.0 * two_pi);
-    else if (C >= two_pi) C = __dsub_rn(C, two_pi);
-    a.c32 = __double2float_rn(C);
-    if (a.c32 >= two_pi_f()) a.c32 = 0.0f;
-  }
-  return a;
-}
-
-__device__ inline void set_sweep_params(DevState *st, uint32_t quant, uint32_t t, double beta,
-                                        const Axis &a) {
-  st->t = t;
-  st->beta = beta;
-  st->cphi = a.c;
-  st->sphi = a.s;
-  st->cphi32 = __double2float_rn(a.c);
-  st->sphi32 = __double2float_rn(a.s);
-  st->c32 = a.c32;
-  st->seed_site = a.seed_site;
-  st->beta2_32 = __double2float_rn(2.0 * beta);
-  // band half-width: 4x the error bound of the FP32 evaluation of u - p;
-  // u16 adds <= 4.2e-7 per projection for the FP32 angle q 2pi_f 2^-16
-  const double dx = quant ? 3.0e-6 : 2.0e-6;
-  st->eps = __double2float_rn(4.0 * (2.0 * beta * dx + 3.0e-7) + 0x1p-24);
-}
-
 // K5: one CTA of two warps per lattice.  Warp 0 reduces the accumulator
 // slots and derives the record and the PCC step; warp 1 meanwhile draws the
 // axis of the next sweep, so the two FP64 chains run on two schedulers at
 // once.  Lane k of warp 0 ends with the sum of entry k over all slots: one
 // FP64 instruction then converts (and one scales) all of them, instead of a
-// serial chain on one lane.
+// serial chain on one lane.  mode 0: the full step, the next parameters in
+// both slots; mode kFinRecord | par: the last record of a fixed-beta call
+// (see kCtlDraw), no axis to draw.
 constexpr int kFinalizeThreads = 64;
 
 static __global__ void __launch_bounds__(kFinalizeThreads)
-    k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep) {
+    k_finalize(const LatDesc *__restrict__ descs, uint32_t nrep, uint32_t mode) {
   const uint32_t rep = blockIdx.x;
   if (rep >= nrep) return;
   // The kernel is a chain of dependent memory accesses (ncu: ~11 us for
@@ -1230,13 +1357,17 @@ static __global__ void __launch_bounds__(kFinalizeThreads)
   pdl_prologue();
   DevState *st = d.st;
   const DevState s0 = *st;
+  const bool record_only = (mode & kFinRecord) != 0u;
+  const uint32_t par = mode & kCtlPar;
+  // selects, not s0.p[par]: a run-time index would put s0 in local memory
+  const SweepParams sp = par ? s0.p[1] : s0.p[0];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ Axis next;
   static_assert(kSlots * kAccStride == 32 * 32 && kAccStride == 16,
                 "the slots read as 32 rows of 32 entries, lane l holding entry l % 16");
-  double nb = s0.beta;  // beta of the next sweep (thread 0)
+  double nb = sp.beta;  // beta of the next sweep (thread 0)
   if (warp == 1) {
-    if (lane == 0) next = draw_axis(s0.quant, s0.t + 1u, d.key0, d.key1, d.L);
+    if (lane == 0 && !record_only) next = draw_axis(s0.quant, sp.t + 1u, d.key0, d.key1, d.L);
   } else {
     // Row i of 32 consecutive entries holds slots 2i and 2i + 1, so lane l
     // reads entry l % 16 of slot 2i + l / 16: every load and store is
@@ -1250,56 +1381,32 @@ static __global__ void __launch_bounds__(kFinalizeThreads)
 #pragma unroll
     for (int i = 0; i < 32; ++i) tot += v[i];
     tot += __shfl_xor_sync(0xFFFFFFFFu, tot, 16);
-    const double x = static_cast<double>(tot) * (1.0 / kFixScale);  // S_k
-    const double y = x * d.inv_n;                                     // S_k / N
-    double sq = (lane >= 6 && lane < 14) ? x * x : 0.0;  // |F|^2 terms of chik
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, off);
-    const double mx = __shfl_sync(0xFFFFFFFFu, y, 0), my = __shfl_sync(0xFFFFFFFFu, y, 1);
-    const double ex = __shfl_sync(0xFFFFFFFFu, y, 2), sx = __shfl_sync(0xFFFFFFFFu, y, 3);
-    const double ey = __shfl_sync(0xFFFFFFFFu, y, 4), sy = __shfl_sync(0xFFFFFFFFu, y, 5);
-    const double x2 = __shfl_sync(0xFFFFFFFFu, x, 2), x4 = __shfl_sync(0xFFFFFFFFu, x, 4);
-    const long long nf = __shfl_sync(0xFFFFFFFFu, tot, kFlipSlot);
-    if (lane == 0) {
-      const double n = static_cast<double>(d.L) * static_cast<double>(d.L);
-      const double beta = s0.beta;
-      ObsRecord o;
-      o.mx = mx;
-      o.my = my;
-      o.m2 = mx * mx + my * my;
-      o.ex = ex;
-      o.sx = sx;
-      o.ey = ey;
-      o.sy = sy;
-      o.energy_per_site = -(x2 + x4) * d.inv_n;
-      o.upsilon = ex - beta * n * sx * sx;  // Eq. (4), J = 1, T = 1/beta
-      o.beta = beta;
-      o.sweep = s0.t;
-      o.chik = sq * (0.5 * d.inv_n);  // 0 unless the lattice measures xi
-      o.flipped = static_cast<uint64_t>(nf);
-      d.rec[s0.rec_count % d.rec_cap] = o;
-      st->rec_count = s0.rec_count + 1;
-      if (s0.pcc_on) {
-        double acc = s0.pcc_acc + beta * o.upsilon;
-        uint32_t count = s0.pcc_count + 1;
-        if (count >= s0.pcc_block) {
-          const double mean = acc / static_cast<double>(s0.pcc_block);
-          double db = s0.pcc_dbeta0;
-          if (s0.pcc_halve) db = ldexp(db, -static_cast<int>(s0.pcc_k / s0.pcc_halve));
-          nb = (mean < s0.pcc_target) ? beta + db : beta - db;
-          acc = 0.0;
-          count = 0;
-        }
-        st->pcc_acc = acc;
-        st->pcc_count = count;
-        st->pcc_k = s0.pcc_k + 1;
+    const ObsRecord o = append_record(d, st, tot, sp.beta, sp.t, s0.rec_count);
+    if (lane == 0 && s0.pcc_on) {
+      const double beta = sp.beta;
+      double acc = s0.pcc_acc + beta * o.upsilon;
+      uint32_t count = s0.pcc_count + 1;
+      if (count >= s0.pcc_block) {
+        const double mean = acc / static_cast<double>(s0.pcc_block);
+        double db = s0.pcc_dbeta0;
+        if (s0.pcc_halve) db = ldexp(db, -static_cast<int>(s0.pcc_k / s0.pcc_halve));
+        nb = (mean < s0.pcc_target) ? beta + db : beta - db;
+        acc = 0.0;
+        count = 0;
       }
+      st->pcc_acc = acc;
+      st->pcc_count = count;
+      st->pcc_k = s0.pcc_k + 1;
     }
   }
   __syncthreads();  // both warps: the next axis from warp 1
   if (threadIdx.x == 0) {
-    st->cur = s0.cur ^ 1u;
-    set_sweep_params(st, s0.quant, s0.t + 1u, nb, next);
+    if (record_only) {
+      st->p[par] = par ? s0.p[0] : s0.p[1];
+    } else {
+      set_sweep_params(&st->p[0], s0.quant, sp.t + 1u, sp.cur ^ 1u, nb, next);
+      st->p[1] = st->p[0];
+    }
   }
 }
 
@@ -1341,7 +1448,6 @@ static __global__ void k_init_wave(LatDesc d) {
 static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   DevState *st = d.st;
   st->quant = quant;
-  st->cur = 0;
   st->pcc_on = 0;
   st->pcc_block = 1;
   st->pcc_halve = 0;
@@ -1354,7 +1460,8 @@ static __global__ void k_init_state(LatDesc d, double beta, uint32_t quant) {
   st->n_fp64 = 0;
   st->n_fp32_wrong = 0;
   st->err = 0;
-  set_sweep_params(st, quant, 0u, beta, draw_axis(quant, 0u, d.key0, d.key1, d.L));
+  set_sweep_params(&st->p[0], quant, 0u, 0u, beta, draw_axis(quant, 0u, d.key0, d.key1, d.L));
+  st->p[1] = st->p[0];
 }
 
 static __global__ void k_set_pcc(DevState *st, uint32_t on, double target,

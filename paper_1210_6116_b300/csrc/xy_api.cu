@@ -62,13 +62,20 @@ struct xy_lattice {
   DevState *d_state;
   uint64_t enqueued;  // sweeps enqueued since xy_init
   bool write_labels = true;  // the next sweep stores canonical labels
+  // how the next sweep is launched: K1's kCtl* bits (0: with k_finalize
+  // after K4), and the k_finalize mode when ctl folds it (the call's last
+  // sweep ends with the record-only finalize; the others launch none)
+  uint32_t ctl = 0;
+  bool fin_after = true;
   uint64_t reported;  // sweeps already returned by xy_measure
   int sm_count;
-  // kernel timing: 6 events per sweep bracket its 5 kernels
+  // kernel timing: 6 events per sweep bracket its 5 kernels (the last two
+  // are adjacent where the sweep launched no k_finalize)
   uint32_t prof;       // 0: off; k: time every k-th sweep
   uint64_t prof_count;  // sweeps launched since profiling was enabled
   bool prof_this;       // the sweep being launched is timed
   std::vector<cudaEvent_t> events;
+  std::vector<uint8_t> ev_fin;  // per timed sweep: k_finalize was launched
   size_t ev_used;
 };
 
@@ -100,8 +107,10 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   const LatDesc *dd = h->d_desc;
   const uint32_t *pre = h->d_prefix;
   const LatDesc &one = h->desc;
-  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL, true>, nw, kThreads,
-                      bond_label_smem<TY>(), s, dd, pre, 1u, nw, one)) != cudaSuccess)
+  const uint32_t ctl = h->ctl, par = ctl & kCtlPar;
+  const uint32_t nb1 = nw + ((ctl & kCtlDraw) ? 1u : 0u);  // + block 0 for the fold
+  if ((e = launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL, true>, nb1, kThreads,
+                      bond_label_smem<TY>(), s, dd, pre, 1u, nw, ctl, one)) != cudaSuccess)
     return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
@@ -119,19 +128,24 @@ cudaError_t launch_sweep_t(xy_lattice *h) {
   const bool ext = h->desc.xi || h->desc.wolff;
   if (ext && h->write_labels)
     e = launch_pdl(k_flip_measure<TY, AT, false, true, true, FULL, true>, nw, kThreads,
-                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, par, one);
   else if (ext)
     e = launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL, true>, nw, kThreads,
-                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, par, one);
   else if (h->write_labels)
     e = launch_pdl(k_flip_measure<TY, AT, false, false, true, FULL, true>, nw, kThreads,
-                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, par, one);
   else
     e = launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL, true>, nw, kThreads,
-                   flip_smem<TY>(), s, dd, pre, 1u, nw, one);
+                   flip_smem<TY>(), s, dd, pre, 1u, nw, par, one);
   if (e != cudaSuccess) return e;
   if ((e = mark(h)) != cudaSuccess) return e;
-  if ((e = launch_pdl(k_finalize, 1u, kFinalizeThreads, 0, s, dd, 1u)) != cudaSuccess) return e;
+  if (h->fin_after) {
+    const uint32_t mode = (ctl & kCtlDraw) ? (kFinRecord | par) : 0u;
+    if ((e = launch_pdl(k_finalize, 1u, kFinalizeThreads, 0, s, dd, 1u, mode)) != cudaSuccess)
+      return e;
+  }
+  if (h->prof_this) h->ev_fin.push_back(h->fin_after ? 1 : 0);
   if ((e = mark(h)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -201,13 +215,13 @@ cudaError_t launch_label_only_t(xy_lattice *h) {
   const uint32_t nw = h->lo.ntiles;
   cudaStream_t s = h->stream;
   k_bond_label<TY, float, true, true>
-      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, LatDesc{});
+      <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, 0u, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
   k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   k_compress<TY><<<compress_blocks(nw), kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
   k_flip_measure<TY, float, true>
-      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, LatDesc{});
+      <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, 0u, LatDesc{});
   return cudaGetLastError();
 }
 
@@ -366,8 +380,13 @@ xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps) {
   if (!h) return fail(XY_EINVAL, "handle is NULL");
   NvtxRange range("xy_sweep");
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 0u, 0.0, 0.0, 0u, 1u);
+  // fixed beta: sweep k keeps its parameters in slot k & 1, its K1 draws the
+  // next sweep's and appends the previous sweep's record (kCtlDraw), and only
+  // the last sweep is followed by k_finalize (the last record)
   for (uint32_t k = 0; k < n_sweeps; ++k) {
     h->write_labels = k + 1 == n_sweeps;  // labels of the call's last sweep
+    h->ctl = (k & 1u) | kCtlDraw | (k ? kCtlRecord : 0u);
+    h->fin_after = k + 1 == n_sweeps;
     XY_CUDA(launch_sweep(h));
   }
   XY_CUDA(cudaGetLastError());
@@ -384,8 +403,12 @@ xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p, uint32_t n_sweeps) 
   NvtxRange range("xy_pcc_step");
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 1u, p->target, p->dbeta0, p->halve_every,
                                     p->block);
+  // the next sweep's beta depends on this sweep's record: k_finalize after
+  // every sweep
   for (uint32_t k = 0; k < n_sweeps; ++k) {
     h->write_labels = k + 1 == n_sweeps;  // labels of the call's last sweep
+    h->ctl = 0u;
+    h->fin_after = true;
     XY_CUDA(launch_sweep(h));
   }
   XY_CUDA(cudaGetLastError());
@@ -424,8 +447,8 @@ xy_status xy_get_state(xy_lattice *h, double *beta, uint64_t *sweep) {
   XY_CUDA(cudaStreamSynchronize(h->stream));
   DevState s;
   XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
-  if (beta) *beta = s.beta;
-  if (sweep) *sweep = s.t;
+  if (beta) *beta = s.p[0].beta;
+  if (sweep) *sweep = s.p[0].t;
   return XY_OK;
 }
 
@@ -498,6 +521,7 @@ xy_status xy_profile(xy_lattice *h, int enable) {
   h->prof = static_cast<uint32_t>(enable);
   h->prof_count = 0;
   h->ev_used = 0;
+  h->ev_fin.clear();
   return XY_OK;
 }
 
@@ -506,8 +530,9 @@ xy_status xy_profile_read(xy_lattice *h, xy_kernel_times *out) {
   XY_CUDA(cudaStreamSynchronize(h->stream));
   std::memset(out, 0, sizeof(*out));
   // events come in groups of 6 per sweep
-  for (size_t base = 0; base + 6 <= h->ev_used; base += 6) {
+  for (size_t base = 0, j = 0; base + 6 <= h->ev_used; base += 6, ++j) {
     for (int k = 0; k < XY_NUM_KERNELS; ++k) {
+      if (k == XY_NUM_KERNELS - 1 && !h->ev_fin[j]) continue;  // no k_finalize
       float ms = 0.0f;
       XY_CUDA(cudaEventElapsedTime(&ms, h->events[base + k], h->events[base + k + 1]));
       out->ms[k] += ms;
@@ -523,7 +548,7 @@ xy_status xy_get_angles(xy_lattice *h, void *host_dst) {
   DevState s;
   XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
   const size_t bytes = static_cast<size_t>(h->lo.L) * h->lo.L * h->lo.esize;
-  XY_CUDA(cudaMemcpy(host_dst, h->desc.theta[s.cur], bytes, cudaMemcpyDeviceToHost));
+  XY_CUDA(cudaMemcpy(host_dst, h->desc.theta[s.p[0].cur], bytes, cudaMemcpyDeviceToHost));
   return XY_OK;
 }
 
@@ -540,11 +565,11 @@ xy_status xy_get_spins(xy_lattice *h, float *host_cos, float *host_sin) {
     const uint64_t m = std::min(chunk, n - i0);
     const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((m + 255) / 256, static_cast<uint64_t>(h->sm_count) * 16));
     if (h->cfg.angle_dtype == XY_F32)
-      k_spins<float><<<blocks, 256, 0, h->stream>>>(h->desc, st.cur, i0, m, buf, buf + chunk);
+      k_spins<float><<<blocks, 256, 0, h->stream>>>(h->desc, st.p[0].cur, i0, m, buf, buf + chunk);
     else if (h->cfg.angle_dtype == XY_F16)
-      k_spins<__half><<<blocks, 256, 0, h->stream>>>(h->desc, st.cur, i0, m, buf, buf + chunk);
+      k_spins<__half><<<blocks, 256, 0, h->stream>>>(h->desc, st.p[0].cur, i0, m, buf, buf + chunk);
     else
-      k_spins<uint16_t><<<blocks, 256, 0, h->stream>>>(h->desc, st.cur, i0, m, buf, buf + chunk);
+      k_spins<uint16_t><<<blocks, 256, 0, h->stream>>>(h->desc, st.p[0].cur, i0, m, buf, buf + chunk);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess && host_cos)
@@ -579,7 +604,7 @@ xy_status xy_set_angles(xy_lattice *h, const void *host_src) {
   XY_CUDA(cudaStreamSynchronize(h->stream));
   DevState s;
   XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
-  XY_CUDA(cudaMemcpy(h->desc.theta[s.cur], host_src, n * h->lo.esize, cudaMemcpyHostToDevice));
+  XY_CUDA(cudaMemcpy(h->desc.theta[s.p[0].cur], host_src, n * h->lo.esize, cudaMemcpyHostToDevice));
   return XY_OK;
 }
 
@@ -635,10 +660,10 @@ xy_status xy_get_sites(xy_lattice *h, const uint64_t *host_sites, uint32_t n,
     uint8_t *bd = reinterpret_cast<uint8_t *>(buf + off_b);
     const uint32_t blocks = (n + 255) / 256;
     if (h->cfg.angle_dtype == XY_F32)
-      k_gather_sites<float><<<blocks, 256>>>(h->desc, h->lo.TY, sites, n, st.cur,
+      k_gather_sites<float><<<blocks, 256>>>(h->desc, h->lo.TY, sites, n, st.p[0].cur,
                                              reinterpret_cast<float *>(buf + off_t), lab, bd);
     else
-      k_gather_sites<uint16_t><<<blocks, 256>>>(h->desc, h->lo.TY, sites, n, st.cur,
+      k_gather_sites<uint16_t><<<blocks, 256>>>(h->desc, h->lo.TY, sites, n, st.p[0].cur,
                                                 reinterpret_cast<uint16_t *>(buf + off_t), lab, bd);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -737,7 +762,7 @@ xy_status xy_save(xy_lattice *h, void *host_blob, size_t *bytes) {
   XY_CUDA(cudaStreamSynchronize(h->stream));
   char *p = static_cast<char *>(host_blob);
   CkptHeader hd;
-  std::memcpy(hd.magic, "XYSWCK01", 8);
+  std::memcpy(hd.magic, "XYSWCK02", 8);
   hd.L = h->lo.L;
   hd.dtype = static_cast<uint32_t>(h->cfg.angle_dtype);
   hd.thr = static_cast<uint32_t>(h->cfg.threshold_mode);
@@ -750,7 +775,7 @@ xy_status xy_save(xy_lattice *h, void *host_blob, size_t *bytes) {
   DevState s;
   XY_CUDA(cudaMemcpy(&s, h->d_state, sizeof(s), cudaMemcpyDeviceToHost));
   std::memcpy(p + sizeof(hd), &s, sizeof(s));
-  XY_CUDA(cudaMemcpy(p + sizeof(hd) + sizeof(s), h->desc.theta[s.cur], ab,
+  XY_CUDA(cudaMemcpy(p + sizeof(hd) + sizeof(s), h->desc.theta[s.p[0].cur], ab,
                      cudaMemcpyDeviceToHost));
   *bytes = need;
   return XY_OK;
@@ -764,14 +789,14 @@ xy_status xy_load(xy_lattice *h, const void *host_blob, size_t bytes) {
   const char *p = static_cast<const char *>(host_blob);
   CkptHeader hd;
   std::memcpy(&hd, p, sizeof(hd));
-  if (std::memcmp(hd.magic, "XYSWCK01", 8) != 0) return fail(XY_EINVAL, "not a checkpoint");
+  if (std::memcmp(hd.magic, "XYSWCK02", 8) != 0) return fail(XY_EINVAL, "not a checkpoint");
   if (hd.L != h->lo.L || hd.dtype != static_cast<uint32_t>(h->cfg.angle_dtype) ||
       hd.seed != h->cfg.seed || hd.state_bytes != sizeof(DevState) || hd.angle_bytes != ab)
     return fail(XY_EINVAL, "checkpoint does not match this lattice (L, dtype or seed)");
   DevState s;
   std::memcpy(&s, p + sizeof(hd), sizeof(s));
   XY_CUDA(cudaStreamSynchronize(h->stream));
-  XY_CUDA(cudaMemcpy(h->desc.theta[s.cur], p + sizeof(hd) + sizeof(s), ab,
+  XY_CUDA(cudaMemcpy(h->desc.theta[s.p[0].cur], p + sizeof(hd) + sizeof(s), ab,
                      cudaMemcpyHostToDevice));
   XY_CUDA(cudaMemcpy(h->d_state, &s, sizeof(s), cudaMemcpyHostToDevice));
   XY_CUDA(cudaMemset(h->desc.acc, 0, sizeof(long long) * kSlots * kAccStride));

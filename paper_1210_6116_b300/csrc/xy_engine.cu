@@ -62,7 +62,7 @@ template <int TY, typename AT, bool EXACT, bool FULL>
 void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uint32_t nw,
                 bool ext, cudaStream_t s) {
   launch_pdl(k_bond_label<TY, AT, EXACT, false, FULL>, nw, kThreads, bond_label_smem<TY>(), s, descs,
-             prefix, nrep, nw, LatDesc{});
+             prefix, nrep, nw, 0u, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint64_t eb = (items + kThreads - 1) / kThreads;
   launch_pdl(k_merge<TY, FULL>, static_cast<uint32_t>(eb), kThreads, 0, s, descs, prefix, nrep, nw);
@@ -70,11 +70,11 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
     launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s, descs,
-               prefix, nrep, nw, LatDesc{});
+               prefix, nrep, nw, 0u, LatDesc{});
   else
     launch_pdl(k_flip_measure<TY, AT, false, false, false, FULL>, nw, kThreads, flip_smem<TY>(), s,
-               descs, prefix, nrep, nw, LatDesc{});
-  launch_pdl(k_finalize, nrep, kFinalizeThreads, 0, s, descs, nrep);
+               descs, prefix, nrep, nw, 0u, LatDesc{});
+  launch_pdl(k_finalize, nrep, kFinalizeThreads, 0, s, descs, nrep, 0u);
 }
 
 template <typename AT, bool EXACT, bool FULL>
@@ -334,7 +334,7 @@ xy_status xy_engine_get_angles(xy_engine *e, uint32_t slot, void *host_dst) {
   XY_CUDA(cudaStreamSynchronize(e->stream));
   DevState st;
   XY_CUDA(cudaMemcpy(&st, s.desc.st, sizeof(st), cudaMemcpyDeviceToHost));
-  XY_CUDA(cudaMemcpy(host_dst, s.desc.theta[st.cur],
+  XY_CUDA(cudaMemcpy(host_dst, s.desc.theta[st.p[0].cur],
                      static_cast<size_t>(s.lo.L) * s.lo.L * s.lo.esize, cudaMemcpyDeviceToHost));
   return XY_OK;
 }
@@ -345,8 +345,8 @@ xy_status xy_engine_get_state(xy_engine *e, uint32_t slot, double *beta, uint64_
   XY_CUDA(cudaStreamSynchronize(e->stream));
   DevState st;
   XY_CUDA(cudaMemcpy(&st, e->slots[slot].desc.st, sizeof(st), cudaMemcpyDeviceToHost));
-  if (beta) *beta = st.beta;
-  if (sweep) *sweep = st.t;
+  if (beta) *beta = st.p[0].beta;
+  if (sweep) *sweep = st.p[0].t;
   return XY_OK;
 }
 

@@ -1,0 +1,101 @@
+"""Fixed-beta sweeps fold the finalize step into the next sweep's first kernel.
+
+Block 0 of k_bond_label appends the previous sweep's record (Eqs. (3)-(6))
+and draws the next sweep's random axis (Sec. 2). k_finalize then runs only at
+the end of each xy_sweep call. xy_pcc_step with dbeta0 = 0 keeps beta fixed
+but runs the unfolded path, with k_finalize after every sweep. The two must
+give bit-identical angles, labels, records and state. The calls are of 1, 2,
+3 and 4 sweeps, so that a call ends in either parameter slot. The tests also
+mix the two kinds of call on one lattice and cross a save / load. The
+unfolded path is itself checked against the oracle in test_gpu_parity.py.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1210_6116_b300 as xy  # noqa: E402
+from paper_1210_6116_b300 import build as xybuild  # noqa: E402
+
+xybuild.build()
+
+BETA = 1.12
+CALLS = (1, 3, 2, 1, 4)
+CASES = {
+    "f32": dict(L=64),
+    "f32_ragged": dict(L=100, tile_y=32),
+    "f16": dict(L=64, dtype="f16"),
+    "u16": dict(L=64, dtype="u16"),
+    "fp32_thresholds": dict(L=64, exact=False),
+    "xi": dict(L=96, measure_xi=True),
+    "wolff": dict(L=64, update="wolff"),
+}
+
+
+def _pair(kw, seed=77):
+    kw = dict(kw)
+    L = kw.pop("L")
+    return (xy.Lattice(L, BETA, seed, **kw), xy.Lattice(L, BETA, seed, **kw))
+
+
+def _unfolded(lat, n):
+    lat.pcc_step(n, target=0.5, dbeta0=0.0, block=1)
+
+
+def _same(a, b):
+    ra, rb = a.measure(), b.measure()
+    assert len(ra) == len(rb)
+    assert ra.tobytes() == rb.tobytes(), "records differ"
+    assert a.get_angles().tobytes() == b.get_angles().tobytes(), "angles differ"
+    np.testing.assert_array_equal(a.get_labels(), b.get_labels())
+    assert a.state() == b.state()
+    return ra
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fold_matches_finalize(name):
+    a, b = _pair(CASES[name])
+    for n in CALLS:
+        a.sweep(n)
+        _unfolded(b, n)
+    recs = _same(a, b)
+    total = sum(CALLS)
+    assert [int(r["sweep"]) for r in recs] == list(range(total))
+    assert np.all(recs["beta"] == BETA)
+    assert a.state() == (BETA, total)
+
+
+def test_fold_mixed_calls_and_checkpoint():
+    a, b = _pair(CASES["f32_ragged"], seed=5)
+    # fold and unfold alternate on `a`; `b` never folds
+    for n, fold in ((2, True), (1, False), (3, True), (2, False), (1, True)):
+        if fold:
+            a.sweep(n)
+        else:
+            _unfolded(a, n)
+        _unfolded(b, n)
+    _same(a, b)
+    # a checkpoint taken between calls restores both parameter slots
+    blob = a.save()
+    c = xy.Lattice(100, BETA, 5, tile_y=32)
+    c.load(blob)
+    a.sweep(3)
+    c.sweep(3)
+    _same(a, c)
+
+
+def test_fold_profile_counts():
+    lat = xy.Lattice(64, BETA, 9)
+    lat.profile(True, every=1)
+    lat.sweep(3)
+    lat.sweep(1)
+    kt = lat.profile_read()
+    lat.profile(False)
+    assert kt["bond_label"][1] == 4 and kt["flip_measure"][1] == 4
+    assert kt["finalize"][1] == 2  # one record-only finalize per call
+    _unfolded(lat, 2)
+    assert len(lat.measure()) == 6
