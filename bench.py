@@ -212,26 +212,40 @@ def run_ours(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    # kernel durations from every 16th sweep of the timed region: the events
-    # bracketing a sweep's kernels cost it ~12 us, so timing every sweep
-    # would understate the rate by ~4 %
-    lat.profile(True, every=PROFILE_EVERY)
+
+    def sweeps():
+        done = 0
+        while done < args.steps:
+            n = min(1024, args.steps - done)
+            lat.sweep(n)
+            done += n
+
+    # the timed region: the sweeps exactly as a caller runs them
     t_start = time.monotonic()
     ev0.record(stream)
-    done = 0
-    while done < args.steps:
-        n = min(1024, args.steps - done)
-        lat.sweep(n)
-        done += n
+    sweeps()
     ev1.record(stream)
     torch.cuda.synchronize()
     clk.mark(t_start, time.monotonic())
     if pg:
         pg.barrier()
     ms = ev0.elapsed_time(ev1)
+    recs = lat.measure()
+    # kernel durations: a second window of as many sweeps, with CUDA events
+    # around the kernels of every 16th sweep (events between a sweep's kernels
+    # cost it ~12 us, and a timed sweep is launched directly, not replayed
+    # from xy_sweep's chunk graph, so the window runs slower than the first)
+    lat.profile(True, every=PROFILE_EVERY)
+    evp0 = torch.cuda.Event(enable_timing=True)
+    evp1 = torch.cuda.Event(enable_timing=True)
+    evp0.record(stream)
+    sweeps()
+    evp1.record(stream)
+    torch.cuda.synchronize()
     kt = lat.profile_read()
     lat.profile(False)
-    recs = lat.measure()
+    lat.measure(max_records=0)
+    ms_prof = evp0.elapsed_time(evp1)
     value, t_sec = aggregate(pg, ws, N, args.steps, ms / 1e3, device="cuda")
     ms_per_step = t_sec * 1e3 / args.steps
     launches = (xy.LAUNCHES_PER_SWEEP * args.steps
@@ -270,7 +284,10 @@ def run_ours(args):
                                "frac_canon": round(value / ws * M_CANON / peak, 4),
                                "frac_built": round(value / ws * M_BUILT / peak, 4)},
             "kernels": kernels,
-            "kernel_timing": f"CUDA events around the kernels of every {PROFILE_EVERY}th sweep of the timed region",
+            "kernel_timing": (f"CUDA events around the kernels of every {PROFILE_EVERY}th sweep of a "
+                              f"second window of {args.steps} sweeps right after the timed region"),
+            "profiled_window": {"value": round(N * args.steps / (ms_prof * 1e6), 3), "unit": UNIT,
+                                "ms_per_step": round(ms_prof / args.steps, 5)},
             "gpu_launches": launches,
             "last_energy_per_site": float(recs[-1]["energy_per_site"]) if len(recs) else None,
         }

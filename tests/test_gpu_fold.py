@@ -99,3 +99,37 @@ def test_fold_profile_counts():
     assert kt["finalize"][1] == 2  # one record-only finalize per call
     _unfolded(lat, 2)
     assert len(lat.measure()) == 6
+
+
+# ------------------------------------------------------------ chunk graphs
+# xy_sweep replays a recorded CUDA graph of 16 middle sweeps (from an odd
+# sweep index of the call), so calls of >= 18 sweeps go partly through it.
+@pytest.mark.parametrize("name", ["f32", "f32_ragged", "u16", "xi", "wolff"])
+def test_graph_chunks_match_finalize(name):
+    a, b = _pair(CASES[name], seed=11)
+    for n in (40, 18, 35):  # 2, 1 and 2 replays, with direct launches around them
+        a.sweep(n)
+        _unfolded(b, n)
+    assert len(_same(a, b)) == 93
+    # a new descriptor drops the recorded graph; the next call records it again
+    a.set_loop_bound(0)
+    b.set_loop_bound(0)
+    a.sweep(20)
+    _unfolded(b, 20)
+    _same(a, b)
+
+
+def test_graph_chunks_with_profiling():
+    a, b = _pair(CASES["f32"], seed=12)
+    # every 4th sweep timed: every run of 16 holds a timed sweep, no replays
+    a.profile(True, every=4)
+    a.sweep(40)
+    assert a.profile_read()["bond_label"][1] == 10
+    # every 64th: sweep 0 timed, sweeps 1-32 replayed, 33-39 launched directly
+    a.profile(True, every=64)
+    a.sweep(40)
+    kt = a.profile_read()
+    a.profile(False)
+    assert kt["bond_label"][1] == 1 and kt["finalize"][1] == 0
+    _unfolded(b, 80)
+    _same(a, b)
