@@ -67,11 +67,13 @@ struct xy_lattice {
   // sweep ends with the record-only finalize; the others launch none)
   uint32_t ctl = 0;
   bool fin_after = true;
-  // CUDA graph of kChunkSweeps middle sweeps of an xy_sweep call, recorded
-  // on first use on a private stream and replayed on `stream` (null until
-  // then, and again after a change of the descriptor the kernels take)
+  // CUDA graphs of kChunkSweeps sweeps from the middle of a call: [0] for
+  // xy_sweep (folded finalize), [1] for xy_pcc_step (k_finalize after each
+  // sweep).  Recorded on first use on a private stream and replayed on
+  // `stream`; null until then, and again after a change of the descriptor
+  // the kernels take.
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t chunk = nullptr;
+  cudaGraphExec_t chunk[2] = {nullptr, nullptr};
   uint64_t reported;  // sweeps already returned by xy_measure
   int sm_count;
   // kernel timing: 6 events per sweep bracket its 5 kernels (the last two
@@ -227,16 +229,27 @@ void set_fold_sweep(xy_lattice *h, uint32_t k, uint32_t n) {
   h->fin_after = k + 1 == n;
 }
 
-void drop_chunk(xy_lattice *h) {
-  if (h->chunk) cudaGraphExecDestroy(h->chunk);
-  h->chunk = nullptr;
+// Sweep k of an xy_pcc_step call: k_finalize after every sweep (the next
+// beta depends on the record), labels of the last sweep.
+void set_pcc_sweep(xy_lattice *h, uint32_t k, uint32_t n) {
+  h->write_labels = k + 1 == n;
+  h->ctl = 0u;
+  h->fin_after = true;
 }
 
-// Record the chunk graph: kChunkSweeps sweeps from an odd sweep index of a
-// call, none of them the call's last.  The kernels take the descriptor by
-// value and the workspace pointers, all fixed for the handle; a change of
-// the descriptor drops the graph (drop_chunk).
-cudaError_t record_chunk(xy_lattice *h) {
+void drop_chunk(xy_lattice *h) {
+  for (cudaGraphExec_t &g : h->chunk) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+// Record chunk graph `which` (0: xy_sweep, 1: xy_pcc_step): kChunkSweeps
+// sweeps from an odd sweep index of a call, none of them the call's last.
+// The kernels take the descriptor by value and the workspace pointers, all
+// fixed for the handle; a change of the descriptor drops the graphs
+// (drop_chunk).
+cudaError_t record_chunk(xy_lattice *h, int which) {
   cudaError_t e;
   if (!h->cap_stream &&
       (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -250,7 +263,8 @@ cudaError_t record_chunk(xy_lattice *h) {
   h->prof = 0;
   cudaError_t le = cudaSuccess;
   for (uint32_t j = 0; j < kChunkSweeps && le == cudaSuccess; ++j) {
-    set_fold_sweep(h, j + 1u, kChunkSweeps + 2u);
+    if (which == 0) set_fold_sweep(h, j + 1u, kChunkSweeps + 2u);
+    else set_pcc_sweep(h, j + 1u, kChunkSweeps + 2u);
     le = launch_sweep(h, h->cap_stream);
   }
   h->prof = prof;
@@ -261,10 +275,40 @@ cudaError_t record_chunk(xy_lattice *h) {
     if (g) cudaGraphDestroy(g);
     return le != cudaSuccess ? le : e;
   }
-  e = cudaGraphInstantiate(&h->chunk, g, 0);
+  e = cudaGraphInstantiate(&h->chunk[which], g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) h->chunk = nullptr;
+  if (e != cudaSuccess) h->chunk[which] = nullptr;
   return e;
+}
+
+// Enqueue sweeps 0 .. n-1 of a call (which = 0: xy_sweep, 1: xy_pcc_step).
+// Runs of kChunkSweeps sweeps from an odd index that end before the call's
+// last sweep replay chunk graph `which`, unless the stream is being
+// captured by the caller or xy_profile would time a sweep of the run; the
+// others are launched directly.
+cudaError_t enqueue_sweeps(xy_lattice *h, uint32_t n, int which) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(h->stream, &cap);
+  if (e != cudaSuccess) return e;
+  const bool graphs = cap == cudaStreamCaptureStatusNone;
+  for (uint32_t k = 0; k < n;) {
+    const bool odd_middle = (k & 1u) && n - 1u - k >= kChunkSweeps;
+    bool timed = false;  // a sweep of the run would be profiled
+    for (uint32_t j = 0; odd_middle && h->prof && j < kChunkSweeps && !timed; ++j)
+      timed = (h->prof_count + j) % h->prof == 0;
+    if (graphs && odd_middle && !timed) {
+      if (!h->chunk[which] && (e = record_chunk(h, which)) != cudaSuccess) return e;
+      if ((e = cudaGraphLaunch(h->chunk[which], h->stream)) != cudaSuccess) return e;
+      h->prof_count += kChunkSweeps;
+      k += kChunkSweeps;
+      continue;
+    }
+    if (which == 0) set_fold_sweep(h, k, n);
+    else set_pcc_sweep(h, k, n);
+    if ((e = launch_sweep(h, h->stream)) != cudaSuccess) return e;
+    ++k;
+  }
+  return cudaSuccess;
 }
 
 // labeling only, from the bond planes already in the workspace
@@ -440,29 +484,8 @@ xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps) {
   k_set_pcc<<<1, 1, 0, h->stream>>>(h->d_state, 0u, 0.0, 0.0, 0u, 1u);
   // fixed beta: sweep k keeps its parameters in slot k & 1, its K1 draws the
   // next sweep's and appends the previous sweep's record (kCtlDraw), and only
-  // the last sweep is followed by k_finalize (the last record).  Runs of
-  // kChunkSweeps middle sweeps (from an odd k, so on the graph's slots)
-  // replay the chunk graph, unless the stream is being captured by the
-  // caller or a sweep of the run would be timed by xy_profile.
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  XY_CUDA(cudaStreamIsCapturing(h->stream, &cap));
-  const bool graphs = cap == cudaStreamCaptureStatusNone;
-  for (uint32_t k = 0; k < n_sweeps;) {
-    const bool odd_middle = (k & 1u) && n_sweeps - 1u - k >= kChunkSweeps;
-    bool timed = false;  // a sweep of the run would be profiled
-    for (uint32_t j = 0; odd_middle && h->prof && j < kChunkSweeps && !timed; ++j)
-      timed = (h->prof_count + j) % h->prof == 0;
-    if (graphs && odd_middle && !timed) {
-      if (!h->chunk) XY_CUDA(record_chunk(h));
-      XY_CUDA(cudaGraphLaunch(h->chunk, h->stream));
-      h->prof_count += kChunkSweeps;
-      k += kChunkSweeps;
-      continue;
-    }
-    set_fold_sweep(h, k, n_sweeps);
-    XY_CUDA(launch_sweep(h, h->stream));
-    ++k;
-  }
+  // the last sweep is followed by k_finalize (the last record)
+  XY_CUDA(enqueue_sweeps(h, n_sweeps, 0));
   XY_CUDA(cudaGetLastError());
   h->enqueued += n_sweeps;
   return XY_OK;
@@ -479,12 +502,7 @@ xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p, uint32_t n_sweeps) 
                                     p->block);
   // the next sweep's beta depends on this sweep's record: k_finalize after
   // every sweep
-  for (uint32_t k = 0; k < n_sweeps; ++k) {
-    h->write_labels = k + 1 == n_sweeps;  // labels of the call's last sweep
-    h->ctl = 0u;
-    h->fin_after = true;
-    XY_CUDA(launch_sweep(h, h->stream));
-  }
+  XY_CUDA(enqueue_sweeps(h, n_sweeps, 1));
   XY_CUDA(cudaGetLastError());
   h->enqueued += n_sweeps;
   return XY_OK;

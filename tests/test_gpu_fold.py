@@ -133,3 +133,16 @@ def test_graph_chunks_with_profiling():
     assert kt["bond_label"][1] == 1 and kt["finalize"][1] == 0
     _unfolded(b, 80)
     _same(a, b)
+
+
+def test_pcc_graph_chunks_match_direct_launches():
+    # xy_pcc_step replays its own 16-sweep graph; with every sweep timed by
+    # xy_profile all sweeps are launched directly instead
+    a, b = _pair(CASES["f32_ragged"], seed=13)
+    b.profile(True, every=1)
+    for n in (40, 19):
+        for lat in (a, b):
+            lat.pcc_step(n, target=0.6, dbeta0=0.01, halve_every=10, block=3)
+    b.profile(False)
+    recs = _same(a, b)
+    assert len(np.unique(recs["beta"])) > 1  # beta moved
