@@ -285,19 +285,21 @@ cudaError_t record_chunk(xy_lattice *h, int which) {
 // Runs of kChunkSweeps sweeps from an odd index that end before the call's
 // last sweep replay chunk graph `which`, unless the stream is being
 // captured by the caller or xy_profile would time a sweep of the run; the
-// others are launched directly.
+// others are launched directly.  The graph is recorded by the first call of
+// its kind, however short: recording takes the host ~1 ms, which a later,
+// longer call would otherwise spend with the GPU waiting.
 cudaError_t enqueue_sweeps(xy_lattice *h, uint32_t n, int which) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(h->stream, &cap);
   if (e != cudaSuccess) return e;
   const bool graphs = cap == cudaStreamCaptureStatusNone;
+  if (graphs && n && !h->chunk[which] && (e = record_chunk(h, which)) != cudaSuccess) return e;
   for (uint32_t k = 0; k < n;) {
     const bool odd_middle = (k & 1u) && n - 1u - k >= kChunkSweeps;
     bool timed = false;  // a sweep of the run would be profiled
     for (uint32_t j = 0; odd_middle && h->prof && j < kChunkSweeps && !timed; ++j)
       timed = (h->prof_count + j) % h->prof == 0;
     if (graphs && odd_middle && !timed) {
-      if (!h->chunk[which] && (e = record_chunk(h, which)) != cudaSuccess) return e;
       if ((e = cudaGraphLaunch(h->chunk[which], h->stream)) != cudaSuccess) return e;
       h->prof_count += kChunkSweeps;
       k += kChunkSweeps;
