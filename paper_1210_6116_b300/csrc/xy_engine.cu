@@ -112,10 +112,16 @@ struct xy_engine {
   std::vector<uint32_t> order;  // slot of table entry k
   uint32_t nrep = 0, nwork = 0;
   bool dirty = true;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;        // one sweep of every active lattice
+  cudaGraphExec_t exec_chunk = nullptr;  // kEngineChunk such sweeps
 };
 
 namespace {
+
+// Sweeps per replay of the engine's chunk graph.  A chunk keeps the
+// programmatic-launch edges between its sweeps; one graph launch per sweep
+// breaks that chain at every sweep.
+constexpr uint32_t kEngineChunk = 4;
 
 size_t table_bytes(uint32_t max_slots) {
   return align_up(sizeof(LatDesc) * max_slots, 256) + align_up(4u * (max_slots + 1u), 256);
@@ -155,9 +161,9 @@ xy_status rebuild(xy_engine *e) {
   }
   e->nrep = static_cast<uint32_t>(e->order.size());
   e->nwork = e->h_prefix.back();
-  if (e->exec) {
-    cudaGraphExecDestroy(e->exec);
-    e->exec = nullptr;
+  for (cudaGraphExec_t *g : {&e->exec, &e->exec_chunk}) {
+    if (*g) cudaGraphExecDestroy(*g);
+    *g = nullptr;
   }
   e->dirty = false;
   if (e->nrep == 0) return XY_OK;
@@ -166,18 +172,20 @@ xy_status rebuild(xy_engine *e) {
   XY_CUDA(cudaMemcpyAsync(e->d_prefix, e->h_prefix.data(), 4u * (e->nrep + 1u),
                           cudaMemcpyHostToDevice, e->stream));
   XY_CUDA(cudaStreamSynchronize(e->stream));
-  cudaGraph_t graph = nullptr;
-  XY_CUDA(cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal));
-  launch_table(e, e->capture);
-  cudaError_t le = cudaGetLastError();
-  cudaError_t ce = cudaStreamEndCapture(e->capture, &graph);
-  if (le != cudaSuccess || ce != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return fail(XY_ECUDA, "graph capture: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+  for (uint32_t sweeps : {1u, kEngineChunk}) {
+    cudaGraph_t graph = nullptr;
+    XY_CUDA(cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal));
+    for (uint32_t k = 0; k < sweeps; ++k) launch_table(e, e->capture);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(e->capture, &graph);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(XY_ECUDA, "graph capture: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    cudaError_t ie = cudaGraphInstantiate(sweeps == 1u ? &e->exec : &e->exec_chunk, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
   }
-  cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ie != cudaSuccess) return fail(XY_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
   return XY_OK;
 }
 
@@ -288,12 +296,14 @@ xy_status xy_engine_step(xy_engine *e, uint32_t n_sweeps) {
   }
   if (e->nrep == 0 || n_sweeps == 0) return XY_OK;
   nvtxRangePushA("xy_engine_step");
-  for (uint32_t k = 0; k < n_sweeps; ++k) {
-    const cudaError_t ge = cudaGraphLaunch(e->exec, e->stream);
+  for (uint32_t k = 0; k < n_sweeps;) {
+    const bool chunk = n_sweeps - k >= kEngineChunk;
+    const cudaError_t ge = cudaGraphLaunch(chunk ? e->exec_chunk : e->exec, e->stream);
     if (ge != cudaSuccess) {
       nvtxRangePop();
       return fail(XY_ECUDA, "cudaGraphLaunch failed: %s", cudaGetErrorString(ge));
     }
+    k += chunk ? kEngineChunk : 1u;
   }
   nvtxRangePop();
   for (uint32_t k : e->order) e->slots[k].enqueued += n_sweeps;
@@ -354,6 +364,7 @@ xy_status xy_engine_destroy(xy_engine *e) {
   if (!e) return fail(XY_EINVAL, "engine is NULL");
   cudaStreamSynchronize(e->stream);
   if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->exec_chunk) cudaGraphExecDestroy(e->exec_chunk);
   cudaStreamDestroy(e->capture);
   delete e;
   return XY_OK;
