@@ -172,13 +172,17 @@ xy_status xy_init(const xy_config *cfg, void *d_workspace, size_t bytes,
  * xy_obs record to the device ring.  Asynchronous.  The records and the
  * next sweep's random axis are made inside the next sweep's first kernel,
  * and one closing kernel per call makes the last record (4 launches per
- * sweep plus 2 per call). */
+ * sweep plus 2 per call).  Runs of 16 sweeps inside a call replay a CUDA
+ * graph recorded on the handle's private stream at the first call (about
+ * 1 ms of host time, once); while the caller captures the lattice's stream,
+ * or for sweeps that xy_profile times, every kernel is launched directly. */
 xy_status xy_sweep(xy_lattice *h, uint32_t n_sweeps);
 
 /* Enqueue n_sweeps PCC sweeps: each sweep is followed by the PCC rule above.
  * beta lives on the device, so no host round trip happens between sweeps
  * (5 launches per sweep: the record and the beta step need a kernel of
- * their own, because the next sweep's bonds depend on them).
+ * their own, because the next sweep's bonds depend on them).  Runs of 16
+ * sweeps replay a recorded graph as in xy_sweep.
  * XY_EINVAL on NULL params, block = 0, or negative dbeta0. */
 xy_status xy_pcc_step(xy_lattice *h, const xy_pcc_params *p,
                       uint32_t n_sweeps);
@@ -331,7 +335,9 @@ xy_status xy_engine_admit(xy_engine *e, const xy_config *cfg,
                           size_t bytes, uint32_t *slot);
 /* Remove a lattice; its workspace may be reused once this returns. */
 xy_status xy_engine_retire(xy_engine *e, uint32_t slot);
-/* Enqueue n_sweeps sweeps of every active lattice. */
+/* Enqueue n_sweeps sweeps of every active lattice: a recorded graph of 4
+ * sweeps while at least 4 remain, a one-sweep graph for the rest (both
+ * recorded again after an admit or retire). */
 xy_status xy_engine_step(xy_engine *e, uint32_t n_sweeps);
 /* As xy_measure (sync = 1) for one lattice of the engine. */
 xy_status xy_engine_measure(xy_engine *e, uint32_t slot, xy_obs *out,
