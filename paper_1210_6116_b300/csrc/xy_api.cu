@@ -76,8 +76,9 @@ struct xy_lattice {
   cudaGraphExec_t chunk[2] = {nullptr, nullptr};
   uint64_t reported;  // sweeps already returned by xy_measure
   int sm_count;
-  // kernel timing: 6 events per sweep bracket its 5 kernels (the last two
-  // are adjacent where the sweep launched no k_finalize)
+  // kernel timing: 6 events per sweep bracket its kernels, the 5th being
+  // k_finalize (the last two events are adjacent where the sweep launched
+  // none)
   uint32_t prof;       // 0: off; k: time every k-th sweep
   uint64_t prof_count;  // sweeps launched since profiling was enabled
   bool prof_this;       // the sweep being launched is timed

@@ -1,12 +1,14 @@
 // xy_engine.cu -- many independent lattices stepped by shared launches.
 //
 // An engine holds a table of active lattices (slots).  One sweep of all of
-// them is the same five kernels as a single lattice, each launched once for
+// them is the five kernels of a PCC sweep of a single lattice (k_finalize
+// after every sweep: some lattices may run the PCC), each launched once for
 // the whole table: the kernels walk a tile list spanning every lattice and
 // find their lattice by a prefix search, so small lattices share the GPU
-// instead of each paying its own launches.  The five launches are captured in
-// a CUDA graph, replayed once per sweep; the graph is re-captured only when
-// the active set changes (admission or retirement happens between sweeps).
+// instead of each paying its own launches.  The launches are captured in two
+// CUDA graphs, of one sweep and of kEngineChunk sweeps; they are re-captured
+// only when the active set changes (admission or retirement happens between
+// sweeps).
 //
 // Every lattice keeps its own workspace, random numbers (seed, sweep
 // counter), fixed-point observable sums and PCC state, so a lattice's results
