@@ -146,3 +146,23 @@ def test_pcc_graph_chunks_match_direct_launches():
     b.profile(False)
     recs = _same(a, b)
     assert len(np.unique(recs["beta"])) > 1  # beta moved
+
+
+def test_sweep_captured_by_the_caller():
+    # while the caller captures the lattice's stream, xy_sweep launches every
+    # kernel directly (no nested graph); replaying the caller's graph once
+    # advances the lattice like the same call made directly
+    s = torch.cuda.Stream()
+    a = xy.Lattice(64, BETA, 21, stream=s)
+    b = xy.Lattice(64, BETA, 21)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        a.sweep(20)
+    g.replay()
+    torch.cuda.synchronize()
+    b.sweep(20)
+    assert a.get_angles().tobytes() == b.get_angles().tobytes()
+    assert a.state() == b.state() == (BETA, 20)
+    rb = b.measure()
+    ra = a.measure()  # the ring holds the replayed sweeps' records
+    assert ra.tobytes() == rb.tobytes()
