@@ -1010,19 +1010,20 @@ struct EdgeItem {
   bool act;
 };
 
-template <int TY, bool FULL>
+template <int TY, bool FULL, bool ONE>
 __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
                                               const uint32_t *__restrict__ prefix,
-                                              uint32_t nrep, uint32_t nwork, uint64_t item) {
+                                              uint32_t nrep, uint32_t nwork, uint64_t item,
+                                              const LatDesc &one) {
   const uint64_t per = TY + 32;
   const uint64_t total = static_cast<uint64_t>(nwork) * per;  // > 0: launches have work
   const uint64_t it = item < total ? item : total - 1u;
   const uint32_t work = static_cast<uint32_t>(it / per);
   const uint32_t j = static_cast<uint32_t>(it % per);
   EdgeItem e;
-  e.rep = find_rep(prefix, nrep, work);
-  e.d = descs + e.rep;
-  const uint32_t tile = work - __ldg(prefix + e.rep);
+  e.rep = ONE ? 0u : find_rep(prefix, nrep, work);
+  e.d = ONE ? &one : descs + e.rep;
+  const uint32_t tile = ONE ? work : work - __ldg(prefix + e.rep);
   e.tile = tile;
   const bool bond = edge_roots<TY, FULL>(*e.d, tile, j, &e.ta, &e.tb);
   e.act = item < total && bond;
@@ -1038,11 +1039,12 @@ __device__ __forceinline__ bool group_leader(unsigned long long key, uint32_t re
 
 // One thread per edge item; the loop over batches of 32 items (warp w of
 // the grid takes batches w, w + W, ...) lets any grid size cover the items.
-template <int TY, bool FULL = false>
+// ONE: a single lattice whose descriptor is the parameter `one`, as in K1.
+template <int TY, bool FULL = false, bool ONE = false>
 __global__ void __launch_bounds__(kThreads)
     k_merge(const LatDesc *__restrict__ descs,
             const uint32_t *__restrict__ prefix, uint32_t nrep,
-            uint32_t nwork) {
+            uint32_t nwork, const __grid_constant__ LatDesc one) {
   pdl_prologue();
   if (nwork == 0u) return;
   const uint64_t total = static_cast<uint64_t>(nwork) * (TY + 32);
@@ -1052,7 +1054,8 @@ __global__ void __launch_bounds__(kThreads)
   // its tile root
   for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kThreads + (threadIdx.x & ~31u);
        base < total; base += stride) {
-    const EdgeItem e = edge_item<TY, FULL>(descs, prefix, nrep, nwork, base + (threadIdx.x & 31u));
+    const EdgeItem e =
+        edge_item<TY, FULL, ONE>(descs, prefix, nrep, nwork, base + (threadIdx.x & 31u), one);
     const unsigned long long key =
         e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
     if (group_leader(key, e.rep) && e.act)
@@ -1086,17 +1089,17 @@ __device__ __forceinline__ void jump(uint32_t *lab, uint64_t n, uint32_t x, DevS
 // One warp per tile (k_compress CTA b holds tiles 8b .. 8b + 7): its lanes
 // take the tile's links j = lane, lane + 32, ... below the tile's count, so
 // tiles that linked nothing cost one load.
-template <int TY>
+template <int TY, bool ONE = false>
 __global__ void __launch_bounds__(kThreads)
     k_compress(const LatDesc *__restrict__ descs,
                const uint32_t *__restrict__ prefix, uint32_t nrep,
-               uint32_t nwork) {
+               uint32_t nwork, const __grid_constant__ LatDesc one) {
   pdl_prologue();
   const uint32_t work = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (work >= nwork) return;
-  const uint32_t rep = find_rep(prefix, nrep, work);
-  const LatDesc &d = descs[rep];
-  const uint32_t tile = work - __ldg(prefix + rep);
+  const uint32_t rep = ONE ? 0u : find_rep(prefix, nrep, work);
+  const LatDesc &d = ONE ? one : descs[rep];
+  const uint32_t tile = ONE ? work : work - __ldg(prefix + rep);
   constexpr uint32_t per = TY + 32;
   const uint32_t count = min(__ldcg(d.link_count + tile), min(d.link_cap, per));
   const uint32_t *links = d.links + static_cast<uint64_t>(tile) * per;

@@ -122,12 +122,12 @@ cudaError_t launch_sweep_t(xy_lattice *h, cudaStream_t s) {
   if ((e = mark(h)) != cudaSuccess) return e;
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint64_t eb = (items + kThreads - 1) / kThreads;
-  if ((e = launch_pdl(k_merge<TY, FULL>, static_cast<uint32_t>(eb), kThreads, 0, s, dd, pre, 1u,
-                      nw)) != cudaSuccess)
+  if ((e = launch_pdl(k_merge<TY, FULL, true>, static_cast<uint32_t>(eb), kThreads, 0, s, dd,
+                      pre, 1u, nw, one)) != cudaSuccess)
     return e;
   if ((e = mark(h)) != cudaSuccess) return e;
-  if ((e = launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, dd, pre, 1u, nw)) !=
-      cudaSuccess)
+  if ((e = launch_pdl(k_compress<TY, true>, compress_blocks(nw), kThreads, 0, s, dd, pre, 1u, nw,
+                      one)) != cudaSuccess)
     return e;
   if ((e = mark(h)) != cudaSuccess) return e;
   // the extended K4 for chik sums or Wolff; canonical labels only for the
@@ -324,8 +324,9 @@ cudaError_t launch_label_only_t(xy_lattice *h) {
       <<<nw, kThreads, bond_label_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, 0u, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
-  k_compress<TY><<<compress_blocks(nw), kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw);
+  k_merge<TY><<<eb, kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw, LatDesc{});
+  k_compress<TY><<<compress_blocks(nw), kThreads, 0, s>>>(h->d_desc, h->d_prefix, 1, nw,
+                                                          LatDesc{});
   k_flip_measure<TY, float, true>
       <<<nw, kThreads, flip_smem<TY>(), s>>>(h->d_desc, h->d_prefix, 1, nw, 0u, LatDesc{});
   return cudaGetLastError();

@@ -67,8 +67,10 @@ void launch_all(const LatDesc *descs, const uint32_t *prefix, uint32_t nrep, uin
              prefix, nrep, nw, 0u, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (TY + 32);
   const uint64_t eb = (items + kThreads - 1) / kThreads;
-  launch_pdl(k_merge<TY, FULL>, static_cast<uint32_t>(eb), kThreads, 0, s, descs, prefix, nrep, nw);
-  launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, descs, prefix, nrep, nw);
+  launch_pdl(k_merge<TY, FULL>, static_cast<uint32_t>(eb), kThreads, 0, s, descs, prefix, nrep, nw,
+             LatDesc{});
+  launch_pdl(k_compress<TY>, compress_blocks(nw), kThreads, 0, s, descs, prefix, nrep, nw,
+             LatDesc{});
   // the engine exposes no labels: K4 never stores them (WL = false)
   if (ext)  // some lattice measures chik or runs Wolff; the others skip both by their flags
     launch_pdl(k_flip_measure<TY, AT, false, true, false, FULL>, nw, kThreads, flip_smem<TY>(), s, descs,

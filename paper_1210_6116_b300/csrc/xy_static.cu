@@ -171,8 +171,9 @@ xy_status xy_label_bonds_static(uint32_t L, const uint8_t *d_right, const uint8_
       <<<nw, kThreads, bond_label_smem<kStaticTile>(), stream>>>(d_desc, d_prefix, 1, nw, 0u, LatDesc{});
   const uint64_t items = static_cast<uint64_t>(nw) * (kStaticTile + 32);
   const uint32_t eb = static_cast<uint32_t>((items + kThreads - 1) / kThreads);
-  k_merge<kStaticTile><<<eb, kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
-  k_compress<kStaticTile><<<compress_blocks(nw), kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw);
+  k_merge<kStaticTile><<<eb, kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw, LatDesc{});
+  k_compress<kStaticTile>
+      <<<compress_blocks(nw), kThreads, 0, stream>>>(d_desc, d_prefix, 1, nw, LatDesc{});
   k_flip_measure<kStaticTile, float, true>
       <<<nw, kThreads, flip_smem<kStaticTile>(), stream>>>(d_desc, d_prefix, 1, nw, 0u, LatDesc{});
   cudaError_t e = cudaGetLastError();
