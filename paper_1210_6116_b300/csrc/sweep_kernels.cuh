@@ -1031,9 +1031,12 @@ __device__ __forceinline__ EdgeItem edge_item(const LatDesc *__restrict__ descs,
   return e;
 }
 
-// true on the lowest lane of each group of lanes holding the same key
+// true on the lowest lane of each group of lanes holding the same key (and
+// lattice: ONE launches have only one)
+template <bool ONE>
 __device__ __forceinline__ bool group_leader(unsigned long long key, uint32_t rep) {
-  const unsigned m = __match_any_sync(0xFFFFFFFFu, key) & __match_any_sync(0xFFFFFFFFu, rep);
+  unsigned m = __match_any_sync(0xFFFFFFFFu, key);
+  if (!ONE) m &= __match_any_sync(0xFFFFFFFFu, rep);
   return (threadIdx.x & 31u) == static_cast<unsigned>(__ffs(m) - 1);
 }
 
@@ -1058,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads)
         edge_item<TY, FULL, ONE>(descs, prefix, nrep, nwork, base + (threadIdx.x & 31u), one);
     const unsigned long long key =
         e.act ? (static_cast<unsigned long long>(e.ta) << 32 | e.tb) : ~0ull;
-    if (group_leader(key, e.rep) && e.act)
+    if (group_leader<ONE>(key, e.rep) && e.act)
       gunion(e.d->label, static_cast<uint64_t>(e.d->L) * e.d->L, e.ta, e.tb, e.d->st, e.d->find_cap,
              e.d->links + static_cast<uint64_t>(e.tile) * (TY + 32u), e.d->link_count + e.tile,
              min(e.d->link_cap, TY + 32u));
