@@ -4,9 +4,9 @@
 // may be scheduled before its predecessor on the stream has finished and
 // waits for it inside the kernel (pdl_prologue in sweep_kernels.cuh, before
 // its first read of mutable data).  That hides the launch and ramp-up of
-// every kernel behind the one before it: at L = 4096 a sweep takes 302 us
-// instead of 314.  Stream capture records the dependencies as programmatic
-// graph edges.
+// every kernel behind the one before it (~12 us per sweep at L = 4096 when
+// it was introduced).  Stream capture records the dependencies as
+// programmatic graph edges.
 #pragma once
 #include <cuda_runtime.h>
 

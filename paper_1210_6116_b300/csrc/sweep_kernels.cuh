@@ -23,7 +23,7 @@
 //                  k_finalize only closes each API call with the last record.
 //
 // Layouts (per lattice, N = L*L, i = y*L + x):
-//   theta[2]  angle double buffer (FP32 or FP16); the sweep reads theta[cur]
+//   theta[2]  angle double buffer (FP32, FP16 or u16); the sweep reads theta[cur]
 //             and writes theta[cur ^ 1], so halo reads never race with flips.
 //   label     N uint32.
 //   rplane,   tile-major bond bit planes: word (tile*TY + r) holds the right
