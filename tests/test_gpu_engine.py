@@ -156,3 +156,20 @@ def test_step64_sizes_batch_equals_alone_and_oracle(orc):
     orc.sw_run(th, 320, 320, 1.1, 901, 0, 4, record=False)
     np.testing.assert_array_equal(eng.get_angles(slots[1]), th)
     eng.close()
+
+
+def test_chunk_graph_steps_equal_single_steps():
+    # xy_engine_step replays a 4-sweep graph while at least 4 sweeps remain:
+    # step(7) (one chunk, three single sweeps) equals seven step(1) calls
+    pcc = xy.xy_pcc_params(target=2 / math.pi, dbeta0=0.01, halve_every=5, block=2)
+    engines = [xy.Engine(4, tile_y=32) for _ in range(2)]
+    slots = []
+    for eng in engines:
+        slots.append([eng.admit(eng.config(L, 1.05, 70 + L), pcc) for L in (32, 64, 96)])
+    engines[0].step(7)
+    for _ in range(7):
+        engines[1].step(1)
+    for sa, sb in zip(*slots):
+        ra, rb = engines[0].measure(sa), engines[1].measure(sb)
+        assert len(ra) == 7 and ra.tobytes() == rb.tobytes()
+        assert engines[0].get_angles(sa).tobytes() == engines[1].get_angles(sb).tobytes()

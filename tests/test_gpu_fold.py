@@ -166,3 +166,19 @@ def test_sweep_captured_by_the_caller():
     rb = b.measure()
     ra = a.measure()  # the ring holds the replayed sweeps' records
     assert ra.tobytes() == rb.tobytes()
+
+
+def test_pcc_captured_by_the_caller():
+    # the same for xy_pcc_step: no nested graph while the caller captures
+    s = torch.cuda.Stream()
+    a = xy.Lattice(64, 1.0, 22, stream=s)
+    b = xy.Lattice(64, 1.0, 22)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        a.pcc_step(20, target=0.6, dbeta0=0.01, block=1)
+    g.replay()
+    torch.cuda.synchronize()
+    b.pcc_step(20, target=0.6, dbeta0=0.01, block=1)
+    assert a.get_angles().tobytes() == b.get_angles().tobytes()
+    assert a.state() == b.state()
+    assert a.measure().tobytes() == b.measure().tobytes()
