@@ -218,9 +218,9 @@ cudaError_t launch_sweep(xy_lattice *h, cudaStream_t s) { return dispatch_dtype(
 cudaError_t set_attrs(xy_lattice *h) { return dispatch_dtype(h, true, nullptr); }
 
 // Sweeps per replay of the chunk graph.  Even, so that every chunk starts
-// on the same parameter slot.  16 is the measured compromise: chunks of 2
-// to 8 gain up to 1 us per sweep at L <= 1024 but lose up to 1 us at
-// L = 4096, and chunks of 64 lose 2 us at L = 512.
+// on the same parameter slot.  With K1 and K4 triggering their dependent
+// launches after their waits, chunks of 8 to 64 sweeps time within 0.3 us
+// per sweep of each other at L = 256 .. 4096.
 constexpr uint32_t kChunkSweeps = 16;
 
 // Sweep k of an xy_sweep call: the parameter slot k & 1, the record of the
