@@ -802,6 +802,7 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
       // band starts on an even row, so row k uses words 0 and 1 of the draw
       // made at k for even k, words 2 and 3 of that draw for odd k.
       uint32_t Rws[B], Dws[B], Cws[B];
+      uint32_t amb = 0u;  // exact mode: bit 2k (2k + 1) = right (down) bond of row k in the band
       Words4 rn = {0u, 0u, 0u, 0u};
 #pragma unroll
       for (int k = 0; k < B; ++k) {
@@ -814,7 +815,6 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
         if (static_cast<uint32_t>(lane) + 1u == g.w) a_r = a_c;
         bool br = false, bd = false, cn = false;
         if (col_ok) {
-          const uint32_t i = gy * L + g.x0 + lane;
           if ((k & 1) == 0)
             rn = philox4x32_10((gy >> 1) * L + g.x0 + lane, 0u, t, kDomBond, d.key0, d.key1);
           const uint32_t w_r = (k & 1) ? rn.w2 : rn.w0, w_d = (k & 1) ? rn.w3 : rn.w1;
@@ -830,33 +830,52 @@ __global__ void __launch_bounds__(kThreads, (k1_min_blocks<TY, EXACT, FROM_PLANE
           br = u0 < pr;
           bd = u1 < pd;
           if (EXACT) {
-            const bool amb_r = fabsf(u0 - pr) <= eps, amb_d = fabsf(u1 - pd) <= eps;
-            if (amb_r || amb_d) {
-              if (amb_r) {
-                // right neighbour's stored angle (reloaded: this path is rare)
-                const float th_r = (static_cast<uint32_t>(lane) + 1u == g.w)
-                                       ? load_angle(th, static_cast<uint64_t>(gy) * L + g.xh)
-                                       : load_angle(th, static_cast<uint64_t>(i) + 1u);
-                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(th_r), w_r,
-                                         sp.beta, sp.cphi, sp.sphi);
-                atomicAdd(&st->n_fp64, 1ull);
-                if (e != br) atomicAdd(&st->n_fp32_wrong, 1ull);
-                br = e;
-              }
-              if (amb_d) {
-                const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(tv[k + 1]), w_d,
-                                         sp.beta, sp.cphi, sp.sphi);
-                atomicAdd(&st->n_fp64, 1ull);
-                if (e != bd) atomicAdd(&st->n_fp32_wrong, 1ull);
-                bd = e;
-              }
-            }
+            // inside the band the FP32 decision may be wrong: settled below
+            amb |= (fabsf(u0 - pr) <= eps ? 1u : 0u) << (2 * k);
+            amb |= (fabsf(u1 - pd) <= eps ? 2u : 0u) << (2 * k);
           }
           cn = (w_r & 1u) != 0u;  // the coin: bit 0 of the right-bond word
         }
         Rws[k] = __ballot_sync(0xFFFFFFFFu, br);
         Dws[k] = __ballot_sync(0xFFFFFFFFu, bd);
         Cws[k] = __ballot_sync(0xFFFFFFFFu, cn);
+      }
+      // exact mode: the bonds inside the FP32 error band (~3e-5 of them),
+      // recomputed in FP64 with the oracle's operation order.  Kept out of
+      // the loop above, whose registers it would otherwise crowd; the row's
+      // Philox draw is made again and the right neighbour's angle reloaded.
+      if (EXACT && __any_sync(0xFFFFFFFFu, amb != 0u)) {
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const uint32_t m2 = (amb >> (2 * k)) & 3u;
+          if (!__any_sync(0xFFFFFFFFu, m2 != 0u)) continue;
+          bool br = (Rws[k] >> lane) & 1u, bd = (Dws[k] >> lane) & 1u;
+          if (m2) {
+            const uint32_t gy = g.y0 + r0 + k;
+            const Words4 w =
+                philox4x32_10((gy >> 1) * L + g.x0 + lane, 0u, t, kDomBond, d.key0, d.key1);
+            if (m2 & 1u) {
+              const float th_r =
+                  (static_cast<uint32_t>(lane) + 1u == g.w)
+                      ? load_angle(th, static_cast<uint64_t>(gy) * L + g.xh)
+                      : load_angle(th, static_cast<uint64_t>(gy) * L + g.x0 + lane + 1u);
+              const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(th_r),
+                                       (k & 1) ? w.w2 : w.w0, sp.beta, sp.cphi, sp.sphi);
+              atomicAdd(&st->n_fp64, 1ull);
+              if (e != br) atomicAdd(&st->n_fp32_wrong, 1ull);
+              br = e;
+            }
+            if (m2 & 2u) {
+              const bool e = bond_fp64(angle_f64<AT>(tv[k]), angle_f64<AT>(tv[k + 1]),
+                                       (k & 1) ? w.w3 : w.w1, sp.beta, sp.cphi, sp.sphi);
+              atomicAdd(&st->n_fp64, 1ull);
+              if (e != bd) atomicAdd(&st->n_fp32_wrong, 1ull);
+              bd = e;
+            }
+          }
+          Rws[k] = __ballot_sync(0xFFFFFFFFu, br);
+          Dws[k] = __ballot_sync(0xFFFFFFFFu, bd);
+        }
       }
       // one store per plane for the whole band: lane k writes row r0 + k
       {
