@@ -209,6 +209,17 @@ template <>
 __device__ __forceinline__ uint16_t store_value<uint16_t>(float v) {
   return static_cast<uint16_t>(static_cast<uint32_t>(v));  // v is an exact q
 }
+// the storage word of a raw value that is already in the storage format and
+// in range (a loaded angle, or a reflected one from reflect below): no
+// rounding or wrap left to do
+template <typename AT>
+__device__ __forceinline__ AT store_exact(float raw) {
+  return store_value<AT>(raw);
+}
+template <>
+__device__ __forceinline__ __half store_exact<__half>(float raw) {
+  return __float2half_rn(raw);  // exact: raw is a half value
+}
 
 // Kernels hold every stored angle as a float that equals the stored value
 // exactly ("raw": the FP32 angle, the FP16 angle widened, or u16's q).  The
@@ -1269,9 +1280,9 @@ __global__ void __launch_bounds__(kThreads, EXT ? 4 : 5)
       if (f[k]) {
         nv = reflect<AT>(t[k], c32);
         if (static_cast<uint32_t>(k) < nb && col_ok)
-          thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_value<AT>(nv);
+          thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_exact<AT>(nv);
       } else if (static_cast<uint32_t>(k) < nb && col_ok) {
-        thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_value<AT>(t[k]);
+        thout[static_cast<uint64_t>(g.y0 + r0 + k) * L + g.x0 + lane] = store_exact<AT>(t[k]);
       }
       sin_cos<AT>(nv, &sn[k], &co[k]);
     }
