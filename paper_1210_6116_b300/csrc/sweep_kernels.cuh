@@ -272,16 +272,9 @@ __device__ __forceinline__ float reflect<uint16_t>(float raw, float c) {
 // Absolute error <= 1e-7 for both (the tests measure it against FP64); the
 // SFU's __sincosf (~3.6e-7) is not accurate enough for the observable
 // tolerances.
-__device__ __forceinline__ void sincos_cw(float x, float *s, float *c) {
-  constexpr float kTwoOverPi = 0x1.45f306p-1f;  // float nearest 2/pi
-  constexpr float kP1 = 0x1.921fb6p+0f;         // float nearest pi/2
-  constexpr float kP2 = -0x1.777a5cp-25f;       // float nearest pi/2 - kP1
-  constexpr float kRound = 0x1.8p23f;           // 1.5 2^23: adds round to integers
-  const float t = fmaf(x, kTwoOverPi, kRound);   // kRound + q
-  const float q = t - kRound;                    // exact
-  const uint32_t iq = __float_as_uint(t);        // low bits: q mod 4
-  float r = fmaf(-q, kP1, x);
-  r = fmaf(-q, kP2, r);
+// The polynomials at the reduced argument r (|r| <= pi/4), moved to quadrant
+// iq mod 4: (sin, cos)(r + iq pi/2).
+__device__ __forceinline__ void sincos_quadrant(float r, uint32_t iq, float *s, float *c) {
   const float r2 = r * r;
   float ps = fmaf(r2, -0x1.98da66p-13f, 0x1.1105b4p-7f);  // S2 r^2 + S1
   ps = fmaf(ps, r2, -0x1.55554p-3f);                      // .. + S0
@@ -295,13 +288,33 @@ __device__ __forceinline__ void sincos_cw(float x, float *s, float *c) {
   *s = __uint_as_float(__float_as_uint(odd ? cr : sr) ^ ((iq & 2u) << 30));
   *c = __uint_as_float(__float_as_uint(odd ? sr : cr) ^ (((iq + 1u) & 2u) << 30));
 }
+__device__ __forceinline__ void sincos_cw(float x, float *s, float *c) {
+  constexpr float kTwoOverPi = 0x1.45f306p-1f;  // float nearest 2/pi
+  constexpr float kP1 = 0x1.921fb6p+0f;         // float nearest pi/2
+  constexpr float kP2 = -0x1.777a5cp-25f;       // float nearest pi/2 - kP1
+  constexpr float kRound = 0x1.8p23f;           // 1.5 2^23: adds round to integers
+  const float t = fmaf(x, kTwoOverPi, kRound);   // kRound + q
+  const float q = t - kRound;                    // exact
+  float r = fmaf(-q, kP1, x);
+  r = fmaf(-q, kP2, r);
+  sincos_quadrant(r, __float_as_uint(t), s, c);  // the low bits of t: q mod 4
+}
 template <typename AT>
 __device__ __forceinline__ void sin_cos(float raw, float *s, float *c) {
   sincos_cw(raw, s, c);
 }
 template <>
 __device__ __forceinline__ void sin_cos<uint16_t>(float raw, float *s, float *c) {
-  sincospif(raw * 0x1p-15f, s, c);  // q 2^-15 is exact: sin(pi q / 32768)
+  // angle q 2pi / 65536 = n pi/2 + m pi/32768 with n the nearest integer to
+  // q / 16384 and |m| <= 8192, both exact integers; r = m pi/32768 by one
+  // FMA over pi/32768 split in two floats (sincos_cw's P1, P2 times 2^-14):
+  // within ~3e-8 of the exact remainder, and over all 65536 q the result is
+  // within 6.5e-8 of FP64 cos and sin
+  const int q = static_cast<int>(raw);
+  const int n = (q + 8192) >> 14;
+  const float m = static_cast<float>(q - (n << 14));
+  const float r = fmaf(m, 0x1.921fb6p-14f, m * -0x1.777a5cp-39f);
+  sincos_quadrant(r, static_cast<uint32_t>(n), s, c);
 }
 
 // projection s.r in FP32 from the stored angle; sin/cos through the SFU on
