@@ -173,6 +173,26 @@ def test_chain_ragged_exact(orc, L, ty):
     np.testing.assert_array_equal(lat.get_angles(), th)
 
 
+def test_fp16_bench_size_one_sweep(orc):
+    """L = 4096, tile 64, one FP16 sweep from the random start (the
+    benchmark's path with FP16 storage): bonds, labels, the stored halves of
+    the flipped configuration and its observables."""
+    L, beta, seed = 4096, 1.12, 1005
+    lat = _lat(L, beta, seed, tile_y=64, dtype="f16")
+    h0 = orc.init_angles(L, seed, 0, dtype=np.float16)
+    lat.sweep(1)
+    rec = lat.measure()
+    g_r, g_d = lat.get_bonds()
+    o_r, o_d, band = orc.bonds(h0, L, L, beta, seed, 0)
+    assert int((g_r != o_r).sum() + (g_d != o_d).sum()) <= band
+    g_lab = lat.get_labels()
+    np.testing.assert_array_equal(g_lab, orc.label_bfs(g_r, g_d, L, L)[0])
+    h = h0.copy()
+    orc.flip(h, g_lab, L, L, seed, 0, orc.axis(seed, 0)[4])
+    np.testing.assert_array_equal(lat.get_angles().view(np.uint16), h.view(np.uint16))
+    assert not obs_close(rec_dict(rec[0]), orc.measure(h, L, L, beta), L * L, beta)
+
+
 def test_fp16_chain_bit_exact(orc):
     L, beta, seed = 80, 1.1, 5
     lat = _lat(L, beta, seed, dtype="f16", tile_y=32)
